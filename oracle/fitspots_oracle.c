@@ -1,0 +1,425 @@
+/*
+ * FP64 oracle for implicit-amplitude Levenberg-Marquardt fitting of 2-D Gaussian
+ * spots (Leutenegger & Weber, "Least-squares fitting of Gaussian spots on graphics
+ * processing units", arXiv 2106.02045).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain, obviously-correct CPU
+ * statement of what the GPU path computes. Only the test suite, the smoke check and
+ * the benchmark's CPU-baseline leg may load it. It shares no code, header, table or
+ * constant with the CUDA library; the two agree only through the paper.
+ *
+ * Everything is double precision and per spot, in the paper's order:
+ *   profile f_i(p) and its derivatives ............ Eq. 10, Eq. 11 (elliptic: by analogy)
+ *   sums F, G, F(bold), G(bold) ................... Eq. 5
+ *   implicit amplitudes alpha^, beta^ ............. Eq. 6
+ *   squared error chi^2 ........................... Eq. 2
+ *   derivative sums and gamma_j ................... Eq. 7
+ *   amplitude derivatives d alpha^/dp, d beta^/dp . Eq. 8
+ *   per-pixel Jacobian J_ij = dh_i/dp_j ........... second factor of Eq. 9
+ *   damped normal equations ....................... Eq. 12, Eq. 14 (J^T J, J^T (g - h))
+ *   damping schedule, stop criteria ............... Sec. "Levenberg-Marquardt algorithm",
+ *                                                   the Fit2DGaussian listing (Sec.
+ *                                                   "Implementation") and the criteria of
+ *                                                   Sec. "Results and Discussion".
+ * The Jacobian is formed explicitly pixel by pixel (Eq. 9 form); no sum expansion.
+ *
+ * Readings where the paper is silent or garbled (each one also listed in the design doc):
+ *   R1  Eq. 12 sign: J = dh/dp, right-hand side J^T (g - h), p' = p + delta.
+ *   R2  Eq. 13 "Jacobian" is the per-pixel J_ij = dh_i/dp_j; J^T J is P x P.
+ *   R3  inside the lambda-escalation loop the re-evaluated error is the trial error.
+ *   R4  the listing's "NotConverged" after that loop is split: a step below minStep
+ *       without decrease -> NO_DECREASE (converged class); otherwise NOT_CONVERGED.
+ *   R6  minStep is relative: |delta_j| < min_step * |best_j| (benchmark criterion iii).
+ *   R7  maxError ("A/3") is an absolute, caller-supplied chi^2 threshold.
+ *   R8  limit(): x in [-0.5, W-0.5], y in [-0.5, H-0.5], each sigma in [0.25, max(W,H)].
+ *   R9  normalised chi^2 = chi^2 / (N - P - 2).
+ *   R10 stop tests after an accepted step in the order MAX_ERROR, MIN_DELTA, MIN_STEP;
+ *       a trial error equal to the best error is accepted (and then meets MIN_DELTA).
+ *   R11 lambda = 10^k with integer k, k = -2 at the start of each fit; "lambda < 10^4"
+ *       is k < 4 (exactly the paper's schedule, free of rounding in the comparison).
+ *   R12 the elliptic (axis-aligned) model, parameters (x, y, sigma_x, sigma_y).
+ * Pixel i of a W x H spot sits at x_i = i mod W, y_i = floor(i / W) (row-major).
+ *
+ * parity unpinned: limit() bounds (R8), normalised chi^2 (R9), the maxError default
+ * (R7) and the NO_DECREASE split (R4) are conventions; the CUDA path follows the same
+ * readings, nothing in the paper fixes them.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAX_PIXELS 1024
+
+/* spot models */
+#define OR_MODEL_ISO 0
+#define OR_MODEL_ELLIPTIC 1
+/* image element types (the oracle also takes fp64 images for exact-recovery tests) */
+#define OR_U16 0
+#define OR_F32 1
+#define OR_F64 2
+/* per-spot outcome */
+#define OR_MAX_ITER 0
+#define OR_MIN_DELTA 1
+#define OR_MIN_STEP 2
+#define OR_MAX_ERROR 3
+#define OR_NO_DECREASE 4
+#define OR_NOT_CONVERGED (-1)
+#define OR_INVALID (-2)
+
+int or_nparams(int model) { return model == OR_MODEL_ISO ? 3 : 4; }
+
+/* Profile f_i(p) (Eq. 10; elliptic by analogy) and, if d != NULL, its partial
+ * derivatives d[j*N + i] = df_i/dp_j (Eq. 11). */
+void or_profile(int model, int W, int H, const double *p, double *f, double *d)
+{
+    const int N = W * H;
+    for (int i = 0; i < N; ++i) {
+        const double x = (double)(i % W), y = (double)(i / W);
+        const double dx = x - p[0], dy = y - p[1];
+        if (model == OR_MODEL_ISO) {
+            const double s = p[2];
+            const double q = dx * dx + dy * dy;
+            const double fi = exp(-q / (2.0 * s * s));
+            f[i] = fi;
+            if (d) {
+                d[0 * N + i] = dx / (s * s) * fi;
+                d[1 * N + i] = dy / (s * s) * fi;
+                d[2 * N + i] = q / (s * s * s) * fi;
+            }
+        } else {
+            const double sx = p[2], sy = p[3];
+            const double fi = exp(-dx * dx / (2.0 * sx * sx) - dy * dy / (2.0 * sy * sy));
+            f[i] = fi;
+            if (d) {
+                d[0 * N + i] = dx / (sx * sx) * fi;
+                d[1 * N + i] = dy / (sy * sy) * fi;
+                d[2 * N + i] = dx * dx / (sx * sx * sx) * fi;
+                d[3 * N + i] = dy * dy / (sy * sy * sy) * fi;
+            }
+        }
+    }
+}
+
+/* Implicit amplitudes, Eq. 5 and Eq. 6. Returns 0, or -1 when N F(bold) - F^2 is not
+ * positive and finite (no unique solution). */
+int or_amplitudes(int N, const double *f, const double *g, double *alpha, double *beta)
+{
+    double F = 0.0, G = 0.0, FF = 0.0, FG = 0.0;
+    for (int i = 0; i < N; ++i) {
+        F += f[i];
+        G += g[i];
+        FF += f[i] * f[i];
+        FG += f[i] * g[i];
+    }
+    const double D = (double)N * FF - F * F;
+    if (!(D > 0.0) || !isfinite(D)) return -1;
+    *alpha = ((double)N * FG - F * G) / D;
+    *beta = (G * FF - F * FG) / D;
+    return 0;
+}
+
+/* Squared error of Eq. 2 at given amplitudes; r (optional) receives g_i - h_i. */
+double or_chi2(int N, const double *f, const double *g, double alpha, double beta, double *r)
+{
+    double c2 = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double ri = g[i] - (alpha * f[i] + beta);
+        if (r) r[i] = ri;
+        c2 += ri * ri;
+    }
+    return c2;
+}
+
+/* Per-pixel Jacobian J[j*N + i] = dh_i/dp_j of the implicit-amplitude model
+ * h_i = alpha^(p) f_i(p) + beta^(p): the second factor of Eq. 9, with the amplitude
+ * derivatives of Eq. 8 built from the sums of Eq. 7. Also returns alpha^, beta^ and
+ * their derivatives. Returns 0, or -1 if the amplitudes are undefined. */
+int or_jacobian(int model, int W, int H, const double *g, const double *p, double *J,
+                double *alpha, double *beta, double *dalpha, double *dbeta)
+{
+    const int N = W * H, P = or_nparams(model);
+    double f[OR_MAX_PIXELS], d[4 * OR_MAX_PIXELS];
+    or_profile(model, W, H, p, f, d);
+    double a, b;
+    if (or_amplitudes(N, f, g, &a, &b)) return -1;
+    double F = 0.0, G = 0.0, FF = 0.0, FG = 0.0;
+    for (int i = 0; i < N; ++i) {
+        F += f[i];
+        G += g[i];
+        FF += f[i] * f[i];
+        FG += f[i] * g[i];
+    }
+    const double D = (double)N * FF - F * F;
+    for (int j = 0; j < P; ++j) {
+        const double *dj = d + (size_t)j * N;
+        double dF = 0.0, dFF = 0.0, dG = 0.0;           /* Eq. 7 */
+        for (int i = 0; i < N; ++i) {
+            dF += dj[i];
+            dFF += 2.0 * f[i] * dj[i];
+            dG += g[i] * dj[i];
+        }
+        const double gamma = (double)N * dFF - 2.0 * F * dF;
+        const double da = ((double)N * dG - G * dF - a * gamma) / D;            /* Eq. 8 */
+        const double db = (G * dFF - FG * dF - F * dG - b * gamma) / D;
+        if (dalpha) dalpha[j] = da;
+        if (dbeta) dbeta[j] = db;
+        for (int i = 0; i < N; ++i) J[(size_t)j * N + i] = da * f[i] + a * dj[i] + db;
+    }
+    *alpha = a;
+    *beta = b;
+    return 0;
+}
+
+/* One evaluated point: alpha^, beta^, chi^2 and, if A != NULL, the normal equations
+ * A = J^T J and b = J^T (g - h) of Eq. 12. Returns 0, or -1 (amplitudes undefined). */
+static int evaluate(int model, int W, int H, const double *g, const double *p,
+                    double *alpha, double *beta, double *chi2, double A[4][4], double b[4])
+{
+    const int N = W * H, P = or_nparams(model);
+    double f[OR_MAX_PIXELS], r[OR_MAX_PIXELS];
+    if (!A) {
+        or_profile(model, W, H, p, f, NULL);
+        if (or_amplitudes(N, f, g, alpha, beta)) return -1;
+        *chi2 = or_chi2(N, f, g, *alpha, *beta, r);
+        return 0;
+    }
+    double J[4 * OR_MAX_PIXELS];
+    if (or_jacobian(model, W, H, g, p, J, alpha, beta, NULL, NULL)) return -1;
+    or_profile(model, W, H, p, f, NULL);
+    *chi2 = or_chi2(N, f, g, *alpha, *beta, r);
+    for (int j = 0; j < P; ++j) {
+        double bj = 0.0;
+        for (int i = 0; i < N; ++i) bj += J[(size_t)j * N + i] * r[i];
+        b[j] = bj;
+        for (int k = 0; k < P; ++k) {
+            double ajk = 0.0;
+            for (int i = 0; i < N; ++i) ajk += J[(size_t)j * N + i] * J[(size_t)k * N + i];
+            A[j][k] = ajk;
+        }
+    }
+    return 0;
+}
+
+/* Reading R8: clamp a parameter vector to the spot's box. */
+void or_limit(int model, int W, int H, double *p)
+{
+    const double smax = (double)(W > H ? W : H);
+    if (p[0] < -0.5) p[0] = -0.5;
+    if (p[0] > W - 0.5) p[0] = W - 0.5;
+    if (p[1] < -0.5) p[1] = -0.5;
+    if (p[1] > H - 0.5) p[1] = H - 0.5;
+    const int ns = model == OR_MODEL_ISO ? 1 : 2;
+    for (int j = 2; j < 2 + ns; ++j) {
+        if (p[j] < 0.25) p[j] = 0.25;
+        if (p[j] > smax) p[j] = smax;
+    }
+}
+
+/* Eq. 14: delta = (A + lambda diag A)^-1 b by a plain Cholesky factorisation.
+ * Returns 0, or -1 when the damped matrix is not positive definite. */
+static int solve_damped(int P, double A[4][4], const double *b, double lambda, double *delta)
+{
+    double M[4][4], L[4][4] = {{0}}, y[4];
+    for (int j = 0; j < P; ++j)
+        for (int k = 0; k < P; ++k) M[j][k] = A[j][k] + (j == k ? lambda * A[j][j] : 0.0);
+    for (int j = 0; j < P; ++j) {
+        double s = M[j][j];
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        if (!(s > 0.0) || !isfinite(s)) return -1;
+        L[j][j] = sqrt(s);
+        for (int i = j + 1; i < P; ++i) {
+            double t = M[i][j];
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    for (int j = 0; j < P; ++j) {
+        double t = b[j];
+        for (int k = 0; k < j; ++k) t -= L[j][k] * y[k];
+        y[j] = t / L[j][j];
+    }
+    for (int j = P - 1; j >= 0; --j) {
+        double t = y[j];
+        for (int k = j + 1; k < P; ++k) t -= L[k][j] * delta[k];
+        delta[j] = t / L[j][j];
+    }
+    for (int j = 0; j < P; ++j)
+        if (!isfinite(delta[j])) return -1;
+    return 0;
+}
+
+/* The trial point limit(best + delta) and its error; NaN if it cannot be evaluated. */
+static double trial(int model, int W, int H, const double *g, const double *best,
+                    const double *delta, double *pt, double *at, double *bt)
+{
+    const int P = or_nparams(model);
+    pt[0] = best[0] + delta[0];
+    pt[1] = best[1] + delta[1];
+    pt[2] = best[2] + delta[2];
+    pt[3] = P == 4 ? best[3] + delta[3] : pt[2];
+    or_limit(model, W, H, pt);
+    if (P == 3) pt[3] = pt[2];
+    double c2;
+    if (evaluate(model, W, H, g, pt, at, bt, &c2, NULL, NULL)) return NAN;
+    return c2;
+}
+
+static int all_small(int P, const double *delta, const double *best, double min_step)
+{
+    for (int j = 0; j < P; ++j)
+        if (!(fabs(delta[j]) < min_step * fabs(best[j]))) return 0;
+    return 1;
+}
+
+/* One spot: the damped LM loop of Sec. "Levenberg-Marquardt algorithm" with the stop
+ * criteria of the Fit2DGaussian listing. p0 is the caller's start point (4 values; the
+ * isotropic model uses p0[2] as sigma). Outputs p (4 values; isotropic writes sigma
+ * into both slots 2 and 3), alpha^, beta^, normalised chi^2, outcome, iterations and the
+ * number of evaluated points. trace (max_iter + 1 values, or NULL) receives the error at
+ * the start of every iteration followed by the final error; unused slots are NaN. */
+int or_fit_one(int model, int W, int H, const double *g, const double *p0, int max_iter,
+               double max_error, double min_delta, double min_step, double *p_out,
+               double *alpha_out, double *beta_out, double *chi2n_out, int *iters_out,
+               int *evals_out, double *trace)
+{
+    const int P = or_nparams(model);
+    double p[4] = {p0[0], p0[1], p0[2], P == 4 ? p0[3] : p0[2]};
+    or_limit(model, W, H, p);
+    if (P == 3) p[3] = p[2];
+    if (trace)
+        for (int k = 0; k <= max_iter; ++k) trace[k] = NAN;
+
+    int k_lambda = -2; /* lambda = 10^k, initially 0.01 */
+    int it = 0, evals = 0, state = OR_MAX_ITER;
+    double A[4][4], b[4], best[4], delta[4], pt[4];
+
+    while (it < max_iter) {
+        ++it;
+        double a, bb, chi;
+        ++evals;
+        if (evaluate(model, W, H, g, p, &a, &bb, &chi, A, b)) chi = NAN;
+        if (trace) trace[it - 1] = chi;
+        if (isnan(chi)) { state = OR_NOT_CONVERGED; break; }
+        if (chi < max_error) { state = OR_MAX_ERROR; break; }
+        memcpy(best, p, sizeof best);
+
+        double at, btt, Chi;
+        if (solve_damped(P, A, b, pow(10.0, k_lambda), delta)) { state = OR_NOT_CONVERGED; break; }
+        ++evals;
+        Chi = trial(model, W, H, g, best, delta, pt, &at, &btt);
+        if (chi > Chi) --k_lambda;
+        int failed_solve = 0;
+        while (!all_small(P, delta, best, min_step) && chi < Chi && k_lambda < 4) {
+            ++k_lambda;
+            if (solve_damped(P, A, b, pow(10.0, k_lambda), delta)) { failed_solve = 1; break; }
+            ++evals;
+            Chi = trial(model, W, H, g, best, delta, pt, &at, &btt);
+        }
+        if (failed_solve) { state = OR_NOT_CONVERGED; break; }
+        if (chi < Chi || isnan(Chi)) {
+            state = (all_small(P, delta, best, min_step) && !isnan(Chi)) ? OR_NO_DECREASE
+                                                                         : OR_NOT_CONVERGED;
+            break; /* p stays at best */
+        }
+        memcpy(p, pt, sizeof p);
+        if (Chi < max_error) { state = OR_MAX_ERROR; break; }
+        if (chi * (1.0 - min_delta) < Chi) { state = OR_MIN_DELTA; break; }
+        if (all_small(P, delta, best, min_step)) { state = OR_MIN_STEP; break; }
+    }
+
+    /* final error at the reported parameters (the listing's NormalizedChi) */
+    double a, bb, chi;
+    if (evaluate(model, W, H, g, p, &a, &bb, &chi, NULL, NULL)) { a = bb = chi = NAN; }
+    if (trace) trace[it < max_iter ? it : max_iter] = chi;
+    for (int j = 0; j < 4; ++j) p_out[j] = p[j];
+    *alpha_out = a;
+    *beta_out = bb;
+    *chi2n_out = chi / (double)(W * H - P - 2);
+    *iters_out = it;
+    *evals_out = evals;
+    return state;
+}
+
+/* Batch front end with the library's argument layout. images: element buffer of
+ * `dtype`; spot s occupies elements [offsets[s], offsets[s] + W*H) row-major; dims holds
+ * (W, H) per spot; init holds 4 floats per spot. Spots with W < 3, H < 3, W*H > 1024,
+ * W*H <= P + 2, an unknown model or an out-of-range offset get OR_INVALID, their init
+ * parameters back and NaN amplitudes. trace: NULL or n * (max_iter + 1) doubles. */
+void or_fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
+                  const int32_t *dims, const float *init, const uint8_t *model, int64_t n,
+                  int max_iter, double max_error, double min_delta, double min_step,
+                  double *out_params, double *out_alpha, double *out_beta, double *out_chi2,
+                  int32_t *out_state, int32_t *out_iters, int32_t *out_evals, double *trace,
+                  int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < n; ++s) {
+        const int W = dims[2 * s], H = dims[2 * s + 1], m = model[s];
+        const int64_t off = offsets[s];
+        double p0[4] = {init[4 * s], init[4 * s + 1], init[4 * s + 2], init[4 * s + 3]};
+        double *tr = trace ? trace + s * (int64_t)(max_iter + 1) : NULL;
+        const int valid_model = (m == OR_MODEL_ISO || m == OR_MODEL_ELLIPTIC);
+        const int N = W * H;
+        if (!valid_model || W < 3 || H < 3 || N > OR_MAX_PIXELS || N <= or_nparams(m) + 2 ||
+            off < 0 || off + N > image_elems) {
+            for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p0[j];
+            out_alpha[s] = out_beta[s] = out_chi2[s] = NAN;
+            out_state[s] = OR_INVALID;
+            out_iters[s] = 0;
+            if (out_evals) out_evals[s] = 0;
+            if (tr)
+                for (int k = 0; k <= max_iter; ++k) tr[k] = NAN;
+            continue;
+        }
+        double g[OR_MAX_PIXELS];
+        for (int i = 0; i < N; ++i) {
+            if (dtype == OR_U16) g[i] = (double)((const uint16_t *)images)[off + i];
+            else if (dtype == OR_F32) g[i] = (double)((const float *)images)[off + i];
+            else g[i] = ((const double *)images)[off + i];
+        }
+        double p[4], a, b, c2n;
+        int it, ev;
+        const int st = or_fit_one(m, W, H, g, p0, max_iter, max_error, min_delta, min_step, p,
+                                  &a, &b, &c2n, &it, &ev, tr);
+        for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p[j];
+        out_alpha[s] = a;
+        out_beta[s] = b;
+        out_chi2[s] = c2n;
+        out_state[s] = st;
+        out_iters[s] = it;
+        if (out_evals) out_evals[s] = ev;
+    }
+}
+
+/* Pin helper: alpha^, beta^, chi^2 (Eq. 2, 6) and optionally J^T J, J^T (g-h) at p for
+ * one spot given as doubles. Returns 0 or -1. */
+int or_evaluate(int model, int W, int H, const double *g, const double *p, double *alpha,
+                double *beta, double *chi2, double *A16, double *b4)
+{
+    double A[4][4], b[4];
+    const int with_grad = A16 != NULL;
+    if (evaluate(model, W, H, g, p, alpha, beta, chi2, with_grad ? A : NULL, b)) return -1;
+    if (with_grad) {
+        const int P = or_nparams(model);
+        for (int j = 0; j < 4; ++j)
+            for (int k = 0; k < 4; ++k) A16[4 * j + k] = (j < P && k < P) ? A[j][k] : 0.0;
+        for (int j = 0; j < 4; ++j) b4[j] = j < P ? b[j] : 0.0;
+    }
+    return 0;
+}
+
+/* Pin helper: the damped solve of Eq. 14 on a caller-given P x P system. */
+int or_solve_damped(int P, const double *A16, const double *b, double lambda, double *delta)
+{
+    double A[4][4];
+    for (int j = 0; j < 4; ++j)
+        for (int k = 0; k < 4; ++k) A[j][k] = A16[4 * j + k];
+    return solve_damped(P, A, b, lambda, delta);
+}

@@ -1,0 +1,365 @@
+"""Benchmark: converged 2-D Gaussian fits per second on the 32x32 workload.
+
+One step = one batched fit of 1,000,000 spots (32x32 uint16 ROIs, elliptic model, seeded
+synthetic camera data) through ``fit_spots_uniform``, inputs resident in HBM (2 GB, larger
+than L2, so no flush is needed between steps). The JSON line reports:
+
+* value        converged fits per second, kernel timed with CUDA events on its stream
+* e2e          the same metric through the public API from pinned host buffers, with the
+               H2D copy of the step's pixels and start values and the D2H copy of all
+               per-spot results inside the timed region
+* roofline     the fit kernel against the FP32 lane-op peak (152 SMs x 128 lanes x max
+               clock), counting 7 algorithmic FP32 operations per pixel per evaluated
+               point (see the design doc for the derivation)
+* cpu_baseline the FP64 oracle on the host cores, timed on a bounded sample of spots
+
+``--impl reference`` times the oracle itself as the reference arm (host cores only).
+Under torchrun every rank fits its own 1,000,000 spots (weak scaling, no collective on
+the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "converged fits/s at 32x32 ROI (frac of roofline); p50/p99 frame latency"
+UNIT = "fits/s"
+WORKLOAD = "ell32"
+W = H = 32
+N_SPOTS = 1_000_000
+OPS_PER_PIXEL_EVAL = 7          # algorithmic FP32 ops per pixel per evaluated point
+SMS, LANES_PER_SM = 152, 128
+CONVERGED = (1, 2, 3, 4)
+PROFILE = ROOT / "profiles" / "fit_kernel_ell32.md"
+SOURCE = ROOT / "paper_2106_02045_gb300" / "csrc" / "fitspots.cu"
+
+
+def _dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _config(n_gpus: int, n_spots: int = N_SPOTS) -> dict:
+    return {"workload": f"{WORKLOAD}: {n_spots:,} spots per GPU, {W}x{H} uint16 ROIs, elliptic "
+                        "Gaussian, photons log-U(200,20000), background U(50,500)+100, "
+                        "Poisson + 2 e- read noise, LM <= 20 iterations",
+            "global_batch": n_spots * n_gpus, "roi": f"{W}x{H}", "model": "elliptic",
+            "tolerances": {"max_error": 0.0, "min_delta": 1e-6, "min_step": 1e-4},
+            "l2": "inputs (2 GB/GPU) larger than L2; no flush",
+            "parallelism": f"dp{n_gpus}" if n_gpus > 1 else "single GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        try:
+            for line in open(self.path):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) < 7:
+                    continue
+                try:
+                    sm.append(float(f[0]))
+                    mx.append(float(f[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile() -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    if not PROFILE.exists():
+        return None
+    sha = hashlib.sha256(SOURCE.read_bytes()).hexdigest()[:16]
+    per_launch, src = None, None
+    for line in PROFILE.read_text().splitlines():
+        if line.startswith("traffic_bytes_per_full_launch:"):
+            per_launch = float(line.split(":", 1)[1].split()[0])
+        if line.startswith("source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+    return per_launch if (src == sha and per_launch is not None) else None
+
+
+def _cpu_baseline(batch_cpu, n_sample: int) -> dict:
+    import oracle
+    from paper_2106_02045_gb300 import synth
+    import numpy as np
+    sub = batch_cpu
+    d = sub.numpy()
+    img = synth.as_numpy_images(sub)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"], nthreads=cores)
+    dt = time.perf_counter() - t0
+    conv = int(np.isin(ref["state"], CONVERGED).sum())
+    return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample:,} spots of the {WORKLOAD} workload, FP64 oracle, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    """The reference arm: the FP64 oracle on the host cores, same workload and metric."""
+    world, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2106_02045_gb300 import synth
+    n = args.ref_sample
+    b = synth.make_workload(WORKLOAD, n, device="cpu")
+    d = b.numpy()
+    img = synth.as_numpy_images(b)
+    cores = os.cpu_count() or 1
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"], nthreads=cores)
+    times, conv = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"], nthreads=cores)
+        times.append(time.perf_counter() - t0)
+        conv = int(np.isin(r["state"], CONVERGED).sum())
+    tot = sum(times)
+    value = conv * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference", "config": _config(world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
+                             "sample": f"{n:,} spots of the {WORKLOAD} workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run(args) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = _dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02045_gb300 import fitspots, synth
+
+    n_spots = args.spots
+    b = synth.make_workload(WORKLOAD, n_spots, device=dev)
+    if rank > 0:   # each rank its own draw of the workload
+        b = synth.make_ell32(n_spots, seed=synth.SEED_BASE + 2 + 1000 * rank, device=dev)
+    out = fitspots.alloc_outputs(n_spots, dev)
+    ws = torch.empty(max(int(fitspots.library().fit_spots_uniform_workspace()), 16),
+                     dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fitspots.fit_uniform(b.images, W, H, synth.MODEL_ELLIPTIC, b.init, out=out,
+                             workspace=ws, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for e0, e1 in ev:
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        t_all1.record(stream)
+        barrier()
+    clocks = clk.summary()
+    ms_total = t_all0.elapsed_time(t_all1)
+    kernel_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    state = out["state"]
+    conv = int(torch.isin(state, torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())
+    evals = int(out["evals"].sum())
+    launches = args.steps  # one fit kernel per step (plus one workspace memset)
+
+    t = torch.tensor([ms_total, float(conv), float(n_spots)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_job, conv_job = float(tmax[0]), float(tsum[1])
+    else:
+        ms_job, conv_job = ms_total, float(conv)
+    value = conv_job * args.steps / (ms_job * 1e-3)
+
+    # ---------------------------------------------------------------- end to end
+    e2e = _e2e(args, b, out, ws, stream, barrier, world, dev) if not args.no_e2e else None
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    # ---------------------------------------------------------------- roofline
+    kernel_s = statistics.mean(kernel_ms) * 1e-3
+    ops = float(evals) * W * H * OPS_PER_PIXEL_EVAL
+    peak_mhz = 2070.0
+    try:
+        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+        peak_mhz = float(peaks.get("sm_max_mhz", peak_mhz))
+    except (OSError, ValueError):
+        pass
+    peak = SMS * LANES_PER_SM * peak_mhz * 1e6
+    achieved = ops / kernel_s
+    traffic = _traffic_from_profile()
+    if traffic is not None:
+        traffic *= n_spots / N_SPOTS
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "T lane-op/s", "frac": achieved / peak, "traffic": traffic,
+                "ops_per_launch": ops, "evals_per_spot": evals / n_spots,
+                "peak_source": f"derived: {SMS} SMs x {LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz",
+                "kernel": "fit_kernel (uniform 32x32)"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        bcpu = b.head(args.cpu_sample).to("cpu")
+        cpu = _cpu_baseline(bcpu, args.cpu_sample)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_job / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(world, n_spots), "clocks": clocks,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "fits_per_step": n_spots * world, "converged_fraction": conv / n_spots}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _e2e(args, b, out, ws, stream, barrier, world, dev):
+    """The metric through the public API from pinned host buffers, copies included."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2106_02045_gb300 import fitspots, synth
+    h_img = torch.empty(b.images.shape, dtype=b.images.dtype, pin_memory=True)
+    h_img.copy_(b.images)
+    h_init = torch.empty(b.init.shape, dtype=b.init.dtype, pin_memory=True)
+    h_init.copy_(b.init)
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    d_img = torch.empty_like(b.images)
+    d_init = torch.empty_like(b.init)
+
+    def e2e_step():
+        d_img.copy_(h_img, non_blocking=True)
+        d_init.copy_(h_init, non_blocking=True)
+        fitspots.fit_uniform(d_img, W, H, synth.MODEL_ELLIPTIC, d_init, out=out, workspace=ws,
+                             stream=stream)
+        for k in out:
+            h_out[k].copy_(out[k], non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 5))
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    conv_e2e = int(np.isin(h_out["state"].numpy(), CONVERGED).sum())
+    h2d = h_img.numel() * h_img.element_size() + h_init.numel() * h_init.element_size()
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values())
+    te = torch.tensor([e2e_ms, float(conv_e2e)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tm = te.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ts = te.clone()
+        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+        e2e_value = float(ts[1]) / (float(tm[0]) * 1e-3)
+    else:
+        e2e_value = conv_e2e / (e2e_ms * 1e-3)
+
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--spots", type=int, default=N_SPOTS, help="spots per GPU (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

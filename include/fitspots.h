@@ -1,0 +1,152 @@
+/*
+ * fitspots.h -- C ABI of the GB300 (sm_103a) spot-fitting library.
+ *
+ * Batched least-squares fitting of 2-D Gaussian spots with implicit amplitudes
+ * (Leutenegger & Weber, arXiv 2106.02045). For every spot the library minimises
+ *     chi^2(p) = sum_i (alpha^(p) f_i(p) + beta^(p) - g_i)^2            (Eq. 2)
+ * over the shaping parameters p only; the amplitude alpha^ and the background beta^
+ * are the closed-form least-squares solution at each p (Eq. 5-6). The minimiser is the
+ * scale-invariant damped Levenberg-Marquardt iteration of Eq. 12-14 with the damping
+ * schedule and stop criteria of Sec. "Levenberg-Marquardt algorithm" and of the
+ * Fit2DGaussian listing in Sec. "Implementation".
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *images, *offsets, *roi_dims, *init_params, *model, out_* and
+ *     *workspace are DEVICE pointers owned by the caller. The library never allocates,
+ *     frees or retains them past the call's stream work.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *     default stream) and the call returns without synchronising. Outputs are valid
+ *     once the stream has reached that point.
+ *   - Spot s is a W x H row-major block of `images` starting at element offsets[s];
+ *     pixel (x, y) is element offsets[s] + y*W + x, and its centre has coordinates
+ *     (x, y) in the fitted parameters (the first pixel centre is the origin).
+ *   - Parameters are 4 floats per spot: (x0, y0, sigma_x, sigma_y). The isotropic model
+ *     (Eq. 10) reads sigma from slot 2 and writes the fitted sigma into slots 2 and 3.
+ *   - Return value 0 (FS_OK) means the work was enqueued; a negative value means the
+ *     call was rejected before anything was enqueued (see FS_ERR_*), except
+ *     FS_ERR_CUDA, which reports a launch error after earlier work may have been
+ *     enqueued. Per-spot problems never fail a call: they are reported in out_state.
+ */
+#ifndef FITSPOTS_H
+#define FITSPOTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* spot models (one uint8 per spot) */
+#define FS_MODEL_ISO 0      /* exp(-((x-x0)^2+(y-y0)^2)/(2 s^2)), Eq. 10 */
+#define FS_MODEL_ELLIPTIC 1 /* exp(-(x-x0)^2/(2 sx^2) - (y-y0)^2/(2 sy^2)), axis-aligned */
+
+/* pixel element types */
+#define FS_U16 0
+#define FS_F32 1
+
+/* per-spot outcome in out_state (the Fit2DGaussian listing's stop conditions) */
+#define FS_STATE_MAX_ITER 0        /* iteration budget used up, not converged          */
+#define FS_STATE_MIN_DELTA 1       /* converged: chi^2 fell by less than min_delta      */
+#define FS_STATE_MIN_STEP 2        /* converged: every |step_j| < min_step * |p_j|      */
+#define FS_STATE_MAX_ERROR 3       /* converged: chi^2 < max_error                      */
+#define FS_STATE_NO_DECREASE 4     /* converged: step below min_step without decrease   */
+#define FS_STATE_NOT_CONVERGED (-1)/* NaN, singular system, or damping reached 10^4     */
+#define FS_STATE_INVALID_ROI (-2)  /* W or H outside 3..32, W*H<=P+2, bad model/offset */
+
+/* error codes */
+#define FS_OK 0
+#define FS_ERR_NULL (-1)       /* a required pointer is NULL                        */
+#define FS_ERR_SIZE (-2)       /* n < 0, n > 2^31-1 or image_elems < 0              */
+#define FS_ERR_DTYPE (-3)      /* unknown pixel type                                */
+#define FS_ERR_MAX_ITER (-4)   /* max_iter outside [1, 1000]                        */
+#define FS_ERR_TOL (-5)        /* a tolerance is negative or not finite, or          */
+                               /* min_delta >= 1                                     */
+#define FS_ERR_WORKSPACE (-6)  /* workspace smaller than fit_spots_workspace(n)     */
+#define FS_ERR_CUDA (-7)       /* a CUDA call failed; see fit_spots_last_cuda_error  */
+#define FS_ERR_ARG (-8)        /* another argument is out of range                   */
+
+/* Bytes of device workspace that fit_spots needs for n spots (0 for n <= 0). The
+ * workspace holds the spot schedule (size-class counts, cursors and a permutation of
+ * the spot indices); its contents on entry do not matter. */
+size_t fit_spots_workspace(int64_t n);
+
+/* Bytes of device workspace that fit_spots_uniform needs (independent of n). */
+size_t fit_spots_uniform_workspace(void);
+
+/*
+ * Fit n spots.
+ *   images       device, uint16 (FS_U16) or float32 (FS_F32) pixel buffer
+ *   image_elems  number of elements in `images`; spots reaching past it are INVALID
+ *   offsets      device int64[n], element offset of each spot
+ *   roi_dims     device int32[n][2] = (W, H), each in 3..32: at most 1024 pixels per
+ *                spot, the bound of Sec. "Implementation"
+ *   init_params  device float[n][4], start parameters; clamped by limit() first
+ *   model        device uint8[n], FS_MODEL_*
+ *   max_iter     iteration budget, 1..1000 (the paper's benchmark uses 20)
+ *   max_error    absolute chi^2 below which a fit stops (0 disables; the paper's "A/3")
+ *   min_delta    stop when chi^2 falls by less than min_delta * chi^2 (paper: 1e-6)
+ *   min_step     stop when every |step_j| < min_step * |p_j| (paper: 1e-4)
+ *   out_params   device float[n][4] fitted (x0, y0, sigma_x, sigma_y)
+ *   out_alpha    device float[n], amplitude alpha^ at the fitted point (Eq. 6)
+ *   out_beta     device float[n], background beta^ (Eq. 6)
+ *   out_chi2     device float[n], normalised chi^2 = chi^2 / (W*H - P - 2)
+ *   out_state    device int32[n], FS_STATE_*
+ *   out_iters    device int32[n], LM iterations executed
+ *   out_evals    device int32[n] or NULL: points at which the model was evaluated
+ *   workspace    device scratch of at least fit_spots_workspace(n) bytes, 16-byte aligned
+ * Invalid spots get their start parameters back, NaN amplitudes and chi^2, 0 iterations.
+ * Results of a spot depend only on that spot's inputs and the size-class configuration
+ * in force (fit_spots_set_config), never on the other spots of the batch.
+ */
+int fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
+              const int32_t *roi_dims, const float *init_params, const uint8_t *model,
+              int64_t n, int max_iter, double max_error, double min_delta, double min_step,
+              float *out_params, float *out_alpha, float *out_beta, float *out_chi2,
+              int32_t *out_state, int32_t *out_iters, int32_t *out_evals, void *workspace,
+              size_t ws_bytes, void *stream);
+
+/*
+ * Fit n spots of one size and model stored back to back, the layout of the paper's
+ * Fit2DGaussian kernel (one width and pixel count per launch): spot s occupies elements
+ * [s*W*H, (s+1)*W*H) of `images`. One kernel launch, no prepass.
+ *   width, height  W and H, each in 3..32 (FS_ERR_ARG otherwise, or if W*H <= P + 2)
+ *   model_id       FS_MODEL_ISO or FS_MODEL_ELLIPTIC for every spot
+ *   workspace      device scratch of at least fit_spots_uniform_workspace() bytes,
+ *                  16-byte aligned (the work cursor)
+ * Other arguments and the results are as for fit_spots; a spot gives bit-identical
+ * results through either entry point.
+ */
+int fit_spots_uniform(const void *images, int dtype, int width, int height, int model_id,
+                      const float *init_params, int64_t n, int max_iter, double max_error,
+                      double min_delta, double min_step, float *out_params, float *out_alpha,
+                      float *out_beta, float *out_chi2, int32_t *out_state, int32_t *out_iters,
+                      int32_t *out_evals, void *workspace, size_t ws_bytes, void *stream);
+
+/* Message for an FS_ERR_* / FS_OK code (static storage). */
+const char *fit_spots_strerror(int code);
+
+/* The cudaError_t value behind the last FS_ERR_CUDA returned on this thread (0 if none). */
+int fit_spots_last_cuda_error(void);
+
+/*
+ * Size classes and their kernel configurations.
+ * A spot's size class is (ceil(W/8)-1)*4 + (ceil(H/8)-1), i.e. 16 classes for W, H in
+ * 3..32. Each class runs one kernel configuration: `lanes` threads per spot (4, 8, 16
+ * or 32), `cols` ROI columns held by each thread (lanes*cols covers the class's width
+ * bound and stays below the next one), and the class's row bound (8, 16, 24 or 32) as
+ * the per-thread row count. fit_spots_num_configs / fit_spots_config_info
+ * enumerate the compiled configurations; fit_spots_set_config assigns one to a class
+ * (the autotuner's output) and fails with FS_ERR_ARG if it cannot hold the class.
+ */
+int fit_spots_num_classes(void);
+int fit_spots_num_configs(void);
+int fit_spots_config_info(int config, int *lanes, int *cols, int *rows);
+int fit_spots_config_fits(int size_class, int config); /* 1 if usable, else 0 */
+int fit_spots_get_config(int size_class);
+int fit_spots_set_config(int size_class, int config);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FITSPOTS_H */

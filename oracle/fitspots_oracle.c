@@ -38,6 +38,7 @@
  *   R11 lambda = 10^k with integer k, k = -2 at the start of each fit; "lambda < 10^4"
  *       is k < 4 (exactly the paper's schedule, free of rounding in the comparison).
  *   R12 the elliptic (axis-aligned) model, parameters (x, y, sigma_x, sigma_y).
+ *   R13 a ROI is at most 32 x 32 pixels (the paper bounds the pixel count by 1024).
  * Pixel i of a W x H spot sits at x_i = i mod W, y_i = floor(i / W) (row-major).
  *
  * parity unpinned: limit() bounds (R8), normalised chi^2 (R9), the maxError default
@@ -53,6 +54,7 @@
 #endif
 
 #define OR_MAX_PIXELS 1024
+#define OR_MAX_SIDE 32 /* R13: W, H <= 32, so W*H <= 1024 (Sec. "Implementation") */
 
 /* spot models */
 #define OR_MODEL_ISO 0
@@ -346,7 +348,7 @@ int or_fit_one(int model, int W, int H, const double *g, const double *p0, int m
 
 /* Batch front end with the library's argument layout. images: element buffer of
  * `dtype`; spot s occupies elements [offsets[s], offsets[s] + W*H) row-major; dims holds
- * (W, H) per spot; init holds 4 floats per spot. Spots with W < 3, H < 3, W*H > 1024,
+ * (W, H) per spot; init holds 4 floats per spot. Spots with W or H outside 3..32,
  * W*H <= P + 2, an unknown model or an out-of-range offset get OR_INVALID, their init
  * parameters back and NaN amplitudes. trace: NULL or n * (max_iter + 1) doubles. */
 void or_fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
@@ -367,8 +369,8 @@ void or_fit_spots(const void *images, int dtype, int64_t image_elems, const int6
         double *tr = trace ? trace + s * (int64_t)(max_iter + 1) : NULL;
         const int valid_model = (m == OR_MODEL_ISO || m == OR_MODEL_ELLIPTIC);
         const int N = W * H;
-        if (!valid_model || W < 3 || H < 3 || N > OR_MAX_PIXELS || N <= or_nparams(m) + 2 ||
-            off < 0 || off + N > image_elems) {
+        if (!valid_model || W < 3 || H < 3 || W > OR_MAX_SIDE || H > OR_MAX_SIDE ||
+            N <= or_nparams(m) + 2 || off < 0 || off + N > image_elems) {
             for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p0[j];
             out_alpha[s] = out_beta[s] = out_chi2[s] = NAN;
             out_state[s] = OR_INVALID;

@@ -1,0 +1,1116 @@
+// fitspots.cu -- sm_103a kernels and C ABI for batched implicit-amplitude LM fitting of
+// 2-D Gaussian spots (Leutenegger & Weber, arXiv 2106.02045).
+//
+// Work mapping. A spot is held by a group of L threads (L = 4, 8, 16 or 32; 32/L groups
+// per warp). Thread t of a group owns the ROI columns x = t, t+L, ... (C of them) over
+// R rows, with the pixel values in registers for the whole fit. The Gaussian profile of
+// both models separates, f(x, y) = e_x(x) e_y(y) (Eq. 10 and its elliptic extension),
+// so a model evaluation needs W + H exponentials (SFU __expf) instead of W*H, and every
+// per-spot sum of the method is either a product of 1-D moments
+// (F, F(bold), sum d_j, sum f d_j, sum d_j d_k of Eq. 5, 7 and of J^T J) or a bilinear
+// form e_x^T M e_y of a pixel matrix M (the cross-sums with the data). Per pixel and
+// evaluated point that costs 7 FP32 operations:
+//   pass 1 (for Eq. 6):      s(x)  += e_y g'                                    (1)
+//   pass 2 (Eq. 2, 9, 13):   u = g' - (alpha e_x) e_y;  chi += u u;  w = e_y u;
+//                            t0 += w;  t1 += y w;  t2 += y^2 w                  (6)
+// where g' = g - s is the pixel value minus an integer per-spot shift s (kept close to
+// beta^ so that chi^2 = sum (u - beta')^2 does not cancel). Per-thread partial sums are
+// combined with a pairwise tree through shared memory (no atomics, fixed order, so a
+// spot's result does not depend on its neighbours). The LM bookkeeping (Eq. 6 2x2
+// solve, J^T J assembly, diagonally scaled Cholesky of Eq. 14, damping, stop tests) is
+// FP32 and replicated in the group's threads: FP64 runs at about 1/75 of the FP32 rate on
+// this GPU.
+//
+// Gradient. With alpha^, beta^ at their optimum, sum_i r_i = sum_i r_i f_i = 0 (Eq. 4), so
+// J^T r = alpha^ sum_i r_i df_i/dp_j (the other two terms of Eq. 9 vanish), and
+//   J^T J = a R^T + alpha (Fd a^T + D1 b^T) + alpha^2 Ddd
+// with a = d alpha^/dp, b = d beta^/dp (Eq. 8 solved through the 2x2 normal matrix),
+// R_j = sum r df/dp_j, Fd_j = sum f df/dp_j, D1_j = sum df/dp_j, Ddd = sum df df^T.
+//
+// Decisions near a tie. An FP32 chi^2 of ~10^3 terms carries 1e-7..1e-6 relative
+// rounding noise, the order of the stop threshold min_delta (1e-6). When the FP32 change
+// chi_t^2 - chi_b^2 falls within that noise of 0 or of -min_delta * chi_b^2, the
+// group recomputes the change directly as sum dh (dh - 2 r_b) with dh = h_t - h_b formed
+// from the exact parameter difference (expm1 of the exponent difference), so the
+// accept/reject and minimum-decrease tests of the Fit2DGaussian listing are taken on a
+// difference that has relative, not absolute, FP32 error.
+//
+// Scheduling. A prepass sorts spot indices into 16 size classes (ceil(W/8), ceil(H/8));
+// each configuration then runs one persistent launch in which every group pulls spots of
+// its classes from an atomic cursor. A group whose spot has converged loads the next one
+// while the other groups of its warp continue. fit_spots_uniform skips the prepass for
+// batches of equal-size, contiguous spots (the paper's own layout).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "fitspots.h"
+
+namespace {
+
+constexpr int kMaxPixels = 1024;
+constexpr int kMaxSide = 32;
+constexpr int kNumClasses = 16;
+constexpr int kWarpsPerBlock = 4;
+constexpr int K1 = 17;    // first reduction: FG' + 16 one-dimensional moments
+constexpr int K2 = 6;     // second reduction: chi_u, Tf, Tx, Txx, Ty1, Ty2
+constexpr int kTot = 32;  // totals: first (20 slots), second (8), tie refinement (4)
+constexpr float kTieWindow = 5e-7f;
+
+struct FitArgs {
+  const void *images;
+  int dtype;
+  int64_t image_elems;
+  const int64_t *offsets;
+  const int32_t *dims;
+  const float *init;
+  const uint8_t *model;
+  int32_t n;
+  int max_iter;
+  float max_error;
+  float min_delta;
+  float min_step;
+  float *out_params;
+  float *out_alpha;
+  float *out_beta;
+  float *out_chi2;
+  int32_t *out_state;
+  int32_t *out_iters;
+  int32_t *out_evals;
+  // equal-size contiguous batch: spot s is at s*uw*uh, no offsets/dims/model arrays
+  int uniform, uw, uh, umodel;
+  // schedule (workspace)
+  int32_t *counts;   // [16] spots per class
+  int32_t *starts;   // [16] first slot of each class in perm
+  int32_t *cursors;  // [16] next unclaimed item per class
+  int32_t *fill;     // [16] scatter cursors
+  int32_t *perm;     // [n]
+};
+
+// 10^k for the damping factor lambda = 10^k (k = -2 initially); k < -45 gives 0.
+__constant__ float kPow10[50] = {
+    1e-45f, 1e-44f, 1e-43f, 1e-42f, 1e-41f, 1e-40f, 1e-39f, 1e-38f, 1e-37f, 1e-36f,
+    1e-35f, 1e-34f, 1e-33f, 1e-32f, 1e-31f, 1e-30f, 1e-29f, 1e-28f, 1e-27f, 1e-26f,
+    1e-25f, 1e-24f, 1e-23f, 1e-22f, 1e-21f, 1e-20f, 1e-19f, 1e-18f, 1e-17f, 1e-16f,
+    1e-15f, 1e-14f, 1e-13f, 1e-12f, 1e-11f, 1e-10f, 1e-9f,  1e-8f,  1e-7f,  1e-6f,
+    1e-5f,  1e-4f,  1e-3f,  1e-2f,  1e-1f,  1e0f,   1e1f,   1e2f,   1e3f,   1e4f};
+
+__device__ __forceinline__ float pow10i(int k) { return k < -45 ? 0.f : kPow10[min(k, 4) + 45]; }
+
+// ------------------------------------------------------------------ small helpers
+__device__ __forceinline__ int size_class(int W, int H) {
+  return ((W + 7) / 8 - 1) * 4 + ((H + 7) / 8 - 1);
+}
+
+__device__ __forceinline__ bool spot_valid(const FitArgs &a, int s, int &W, int &H, int &m) {
+  W = a.dims[2 * s];
+  H = a.dims[2 * s + 1];
+  m = a.model[s];
+  const int64_t off = a.offsets[s];
+  const int P = (m == FS_MODEL_ISO) ? 3 : 4;
+  return (m == FS_MODEL_ISO || m == FS_MODEL_ELLIPTIC) && W >= 3 && H >= 3 && W <= kMaxSide &&
+         H <= kMaxSide && W * H <= kMaxPixels && W * H > P + 2 && off >= 0 &&
+         off + (int64_t)W * H <= a.image_elems;
+}
+
+__device__ void write_invalid(const FitArgs &a, int s) {
+  for (int j = 0; j < 4; ++j) a.out_params[4 * s + j] = a.init[4 * s + j];
+  a.out_alpha[s] = __int_as_float(0x7fc00000);
+  a.out_beta[s] = __int_as_float(0x7fc00000);
+  a.out_chi2[s] = __int_as_float(0x7fc00000);
+  a.out_state[s] = FS_STATE_INVALID_ROI;
+  a.out_iters[s] = 0;
+  if (a.out_evals) a.out_evals[s] = 0;
+}
+
+// limit(): the box read into the unspecified clamp of the Fit2DGaussian listing,
+// x0 in [-0.5, W-0.5], y0 in [-0.5, H-0.5], each sigma in [0.25, max(W, H)]. Plain
+// comparisons, so a NaN stays NaN (and the spot then reports NOT_CONVERGED).
+__device__ __forceinline__ float clampf(float v, float lo, float hi) {
+  v = (v < lo) ? lo : v;
+  return (v > hi) ? hi : v;
+}
+__device__ __forceinline__ void limit_params(float (&q)[4], int W, int H, bool iso) {
+  const float smax = (float)max(W, H);
+  q[0] = clampf(q[0], -0.5f, (float)W - 0.5f);
+  q[1] = clampf(q[1], -0.5f, (float)H - 0.5f);
+  q[2] = clampf(q[2], 0.25f, smax);
+  q[3] = iso ? q[2] : clampf(q[3], 0.25f, smax);
+}
+
+// 1/s^2, computed the same way wherever a profile is (re)built
+__device__ __forceinline__ float inv_sq(float s) { return __fdividef(1.f, s * s); }
+
+// Eq. 14 with the diagonal scaling that makes the damping scale-invariant:
+// M = S A S has a unit diagonal, (M + lambda I) y = S b, delta = S y. A is packed
+// upper-triangular: A00 A01 A02 A03 A11 A12 A13 A22 A23 A33. Returns false when the
+// damped matrix is not positive definite or the step is not finite.
+__device__ __forceinline__ bool solve_damped(const float (&A)[10], const float (&b)[4], float lam,
+                                             float (&d)[4]) {
+  if (!(A[0] > 0.f) || !(A[4] > 0.f) || !(A[7] > 0.f) || !(A[9] > 0.f)) return false;
+  const float s0 = rsqrtf(A[0]), s1 = rsqrtf(A[4]), s2 = rsqrtf(A[7]), s3 = rsqrtf(A[9]);
+  const float dg = 1.f + lam;
+  const float m01 = A[1] * s0 * s1, m02 = A[2] * s0 * s2, m03 = A[3] * s0 * s3;
+  const float m12 = A[5] * s1 * s2, m13 = A[6] * s1 * s3, m23 = A[8] * s2 * s3;
+  // Cholesky M + lambda I = L L^T, keeping reciprocal pivots r_jj = 1 / L_jj
+  const float r00 = rsqrtf(dg);
+  const float l10 = m01 * r00, l20 = m02 * r00, l30 = m03 * r00;
+  const float p1 = dg - l10 * l10;
+  if (!(p1 > 0.f)) return false;
+  const float r11 = rsqrtf(p1);
+  const float l21 = (m12 - l20 * l10) * r11, l31 = (m13 - l30 * l10) * r11;
+  const float p2 = dg - l20 * l20 - l21 * l21;
+  if (!(p2 > 0.f)) return false;
+  const float r22 = rsqrtf(p2);
+  const float l32 = (m23 - l30 * l20 - l31 * l21) * r22;
+  const float p3 = dg - l30 * l30 - l31 * l31 - l32 * l32;
+  if (!(p3 > 0.f)) return false;
+  const float r33 = rsqrtf(p3);
+  const float z0 = b[0] * s0 * r00;
+  const float z1 = (b[1] * s1 - l10 * z0) * r11;
+  const float z2 = (b[2] * s2 - l20 * z0 - l21 * z1) * r22;
+  const float z3 = (b[3] * s3 - l30 * z0 - l31 * z1 - l32 * z2) * r33;
+  const float y3 = z3 * r33;
+  const float y2 = (z2 - l32 * y3) * r22;
+  const float y1 = (z1 - l21 * y2 - l31 * y3) * r11;
+  const float y0 = (z0 - l10 * y1 - l20 * y2 - l30 * y3) * r00;
+  d[0] = y0 * s0;
+  d[1] = y1 * s1;
+  d[2] = y2 * s2;
+  d[3] = y3 * s3;
+  return isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]) && isfinite(d[3]);
+}
+
+// ------------------------------------------------------------------ group reductions
+// Shared memory of one group: partials red[k*RS + lane] (RS = L + 4 keeps the float4 row
+// reads of a quarter-warp on distinct banks), then kTot totals. The group stride is
+// congruent to L mod 32 so that the groups of a warp write to distinct banks.
+__host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+__host__ __device__ constexpr int red_stride(int L) { return L + 4; }
+__host__ __device__ constexpr int group_stride(int L) {
+  return round_up(K1 * red_stride(L) + kTot, 32) + L;
+}
+// per warp: row tables (R + 1 per group), refinement tables (2R + 2 per group), reductions
+__host__ __device__ constexpr int tab_floats(int L, int R) { return round_up((32 / L) * (R + 1), 4); }
+__host__ __device__ constexpr int rtab_floats(int L, int R) { return round_up((32 / L) * (2 * R + 2), 4); }
+__host__ __device__ constexpr int warp_smem_floats(int L, int R) {
+  return round_up(tab_floats(L, R) + rtab_floats(L, R) + (32 / L) * group_stride(L), 32);
+}
+
+// Pairwise sum of L consecutive floats (16-byte aligned).
+template <int L>
+__device__ __forceinline__ float sum_row(const float *row) {
+  constexpr int Q = L / 4;
+  float s[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float4 v = reinterpret_cast<const float4 *>(row)[i];
+    s[i] = (v.x + v.y) + (v.z + v.w);
+  }
+#pragma unroll
+  for (int step = 1; step < Q; step *= 2)
+#pragma unroll
+    for (int i = 0; i + step < Q; i += 2 * step) s[i] += s[i + step];
+  return s[0];
+}
+
+// Sum K per-thread partials (already stored at red[k*RS + lane]) over the L threads of
+// a group into tot[0..K); on return every thread of the group can read the totals.
+template <int L, int K>
+__device__ __forceinline__ void group_reduce(const float *red, float *tot, int lg, unsigned gmask) {
+  constexpr int RS = red_stride(L);
+  __syncwarp(gmask);
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += L) {
+    const int k = k0 + lg;
+    if (k < K) tot[k] = sum_row<L>(red + k * RS);
+  }
+  __syncwarp(gmask);
+}
+
+template <int L>
+__device__ __forceinline__ float group_sum_shfl(float v, unsigned gmask) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ the fit loop
+struct ClassList {
+  int8_t cls[kNumClasses];
+  int8_t count;
+};
+
+// Persistent kernel for one configuration: L threads per spot, C columns per thread,
+// R rows per thread. It drains the size classes of `cl` in order (or the whole batch of
+// a uniform call).
+template <int L, int C, int R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, ClassList cl) {
+  constexpr int S = 32 / L;
+  constexpr int NR = (R + L - 1) / L;
+  constexpr int TS = R + 1;
+  constexpr int TS2 = 2 * R + 2;
+  constexpr int RS = red_stride(L);
+  constexpr float yc0 = 0.5f * (float)R;  // origin of the row weights y~ = y - R/2
+  static_assert(S * L == 32, "lane groups must tile a warp");
+  extern __shared__ float4 smem4[];
+  float *sw = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * warp_smem_floats(L, R);
+  const int lane = threadIdx.x & 31;
+  const int gi = lane / L, lg = lane % L;
+  const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (gi * L));
+  float *tab = sw + gi * TS;
+  float2 *rtab = reinterpret_cast<float2 *>(sw + tab_floats(L, R) + gi * TS2);
+  float *red = sw + tab_floats(L, R) + rtab_floats(L, R) + gi * group_stride(L);
+  float *tot1 = red + K1 * RS;  // totals of the first reduction (17 used)
+  float *tot2 = tot1 + 20;      // totals of the second reduction (6 used)
+  float *tot3 = tot2 + 8;       // total of the tie refinement
+
+  for (int ci = 0; ci < cl.count; ++ci) {
+    const int cls = cl.cls[ci];
+    const int cnt = a.uniform ? a.n : a.counts[cls];
+    const int beg = a.uniform ? 0 : a.starts[cls];
+
+    float g[C][R];
+    bool active = false, idle = cnt == 0;
+    int spot = 0, W = 0, H = 0, P = 4;
+    bool iso = false;
+    float Nf = 0.f, Gs = 0.f, shift = 0.f;
+    float p[4] = {0.f, 0.f, 1.f, 1.f}, pe[4] = {0.f, 0.f, 1.f, 1.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+    float A[10], bv[4];
+    float chib = 0.f, alb = 0.f, bpb = 0.f, noiseb = 0.f;
+    int klam = -2, it = 0, evals = 0;
+    bool first_eval = false, first_trial = false;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) A[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bv[k] = 0.f;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int y = 0; y < R; ++y) g[c][y] = 0.f;
+
+    while (true) {
+      // -------------------------------------------------------------- refill the slot
+      if (!active && !idle) {
+        int item = 0;
+        if (lg == 0) item = atomicAdd(a.cursors + cls, 1);
+        item = __shfl_sync(gmask, item, gi * L);
+        if (item >= cnt) {
+          idle = true;
+        } else {
+          int64_t off;
+          if (a.uniform) {
+            spot = item;
+            W = a.uw;
+            H = a.uh;
+            iso = a.umodel == FS_MODEL_ISO;
+            off = (int64_t)spot * (W * H);
+          } else {
+            spot = a.perm[beg + item];
+            W = a.dims[2 * spot];
+            H = a.dims[2 * spot + 1];
+            iso = a.model[spot] == FS_MODEL_ISO;
+            off = a.offsets[spot];
+          }
+          P = iso ? 3 : 4;
+          if (a.dtype == FS_U16) {
+            const unsigned short *img = static_cast<const unsigned short *>(a.images) + off;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const int x = lg + L * c;
+#pragma unroll
+              for (int y = 0; y < R; ++y)
+                g[c][y] = (x < W && y < H) ? (float)__ldg(img + y * W + x) : 0.f;
+            }
+          } else {
+            const float *img = static_cast<const float *>(a.images) + off;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const int x = lg + L * c;
+#pragma unroll
+              for (int y = 0; y < R; ++y) g[c][y] = (x < W && y < H) ? __ldg(img + y * W + x) : 0.f;
+            }
+          }
+          // integer shift = corner pixel (a background estimate); refined after pass 1
+          shift = rintf(__shfl_sync(gmask, g[0][0], gi * L));
+          float part = 0.f;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const int x = lg + L * c;
+#pragma unroll
+            for (int y = 0; y < R; ++y) {
+              g[c][y] = (x < W && y < H) ? g[c][y] - shift : 0.f;
+              part += g[c][y];
+            }
+          }
+          Gs = group_sum_shfl<L>(part, gmask);
+          Nf = (float)(W * H);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) pe[j] = a.init[4 * spot + j];
+          limit_params(pe, W, H, iso);
+          klam = -2;
+          it = 0;
+          evals = 0;
+          first_eval = true;
+          active = true;
+        }
+      }
+      if (!__any_sync(0xffffffffu, active)) break;
+      if (!active) continue;
+
+      // -------------------------------------------------------------- evaluate at pe
+      const float sx = pe[2], sy = iso ? pe[2] : pe[3];
+      const float ivx = inv_sq(sx), ivy = inv_sq(sy);
+      const float nhx = -0.5f * ivx, nhy = -0.5f * ivy;
+      float ex[C], dxv[C];
+      {
+        // column profile e_x and the column moments sum dx^m e_x^n
+        float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int x = lg + L * c;
+          const float d = (float)x - pe[0];
+          const float e = (x < W) ? __expf(d * d * nhx) : 0.f;
+          ex[c] = e;
+          dxv[c] = d;
+          const float e2 = e * e, de = d * e, de2 = d * e2;
+          m[0] += e;
+          m[1] += e2;
+          m[2] += de;
+          m[3] = fmaf(d, de, m[3]);
+          m[4] += de2;
+          m[5] = fmaf(d, de2, m[5]);
+          m[6] = fmaf(d * d, de2, m[6]);
+          m[7] = fmaf(d * d * d, de2, m[7]);
+        }
+        // slots: 1 X01, 2 X02, 5 X11, 6 X21, 7 X12, 8 X22, 9 X32, 10 X42
+        red[1 * RS + lg] = m[0];
+        red[2 * RS + lg] = m[1];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[(5 + k) * RS + lg] = m[2 + k];
+      }
+      {
+        // row profile e_y into the group's table, and the row moments
+        float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          const int y = lg + L * k;
+          if (y < R) {
+            const float d = (float)y - pe[1];
+            const float e = (y < H) ? __expf(d * d * nhy) : 0.f;
+            tab[y] = e;
+            const float e2 = e * e, de = d * e, de2 = d * e2;
+            m[0] += e;
+            m[1] += e2;
+            m[2] += de;
+            m[3] = fmaf(d, de, m[3]);
+            m[4] += de2;
+            m[5] = fmaf(d, de2, m[5]);
+            m[6] = fmaf(d * d, de2, m[6]);
+            m[7] = fmaf(d * d * d, de2, m[7]);
+          }
+        }
+        // slots: 3 Y01, 4 Y02, 11 Y11, 12 Y21, 13 Y12, 14 Y22, 15 Y32, 16 Y42
+        red[3 * RS + lg] = m[0];
+        red[4 * RS + lg] = m[1];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[(11 + k) * RS + lg] = m[2 + k];
+      }
+      __syncwarp(gmask);
+      // pass 1: s(x) = sum_y e_y g'(x, y);  FG' partial = sum_x e_x s(x)
+      {
+        float s0[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) s0[c] = 0.f;
+#pragma unroll
+        for (int y = 0; y < R; ++y) {
+          const float e = tab[y];
+#pragma unroll
+          for (int c = 0; c < C; ++c) s0[c] = fmaf(e, g[c][y], s0[c]);
+        }
+        float fg = 0.f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) fg = fmaf(ex[c], s0[c], fg);
+        red[lg] = fg;
+      }
+      group_reduce<L, K1>(red, tot1, lg, gmask);
+      const float4 t1a = reinterpret_cast<const float4 *>(tot1)[0];
+      const float FG = t1a.x, X01 = t1a.y, X02 = t1a.z, Y01 = t1a.w, Y02 = tot1[4];
+      const float F = X01 * Y01, FF = X02 * Y02;
+      const float D = fmaf(Nf, FF, -F * F);
+      const bool okD = D > 0.f && isfinite(D);
+      const float iD = __fdividef(1.f, D);
+      const float alpha = (Nf * FG - F * Gs) * iD;  // Eq. 6
+      float bp = (Gs * FF - F * FG) * iD;           // beta^ - shift
+      if (first_eval && okD) {
+        // move the shift to the integer nearest beta^ (exact for integer pixel values)
+        const float dl0 = rintf(bp);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int x = lg + L * c;
+#pragma unroll
+          for (int y = 0; y < R; ++y) g[c][y] = (x < W && y < H) ? g[c][y] - dl0 : 0.f;
+        }
+        Gs = fmaf(-Nf, dl0, Gs);
+        shift += dl0;
+        bp -= dl0;
+      }
+      // pass 2: u = g' - alpha e_x e_y; chi_u = sum u^2; row-weighted sums of e_y u
+      {
+        float ca[C], ch0[C], ch1[C], t0[C], t1[C], t2[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          ca[c] = -alpha * ex[c];
+          ch0[c] = ch1[c] = t0[c] = t1[c] = t2[c] = 0.f;
+        }
+#pragma unroll
+        for (int y = 0; y < R; ++y) {
+          const float e = tab[y];
+          const float yy = (float)y - yc0;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const float u = fmaf(ca[c], e, g[c][y]);
+            if (y & 1) ch1[c] = fmaf(u, u, ch1[c]);
+            else ch0[c] = fmaf(u, u, ch0[c]);
+            const float w = e * u;
+            t0[c] += w;
+            t1[c] = fmaf(yy, w, t1[c]);
+            t2[c] = fmaf(yy * yy, w, t2[c]);
+          }
+        }
+        float v2[K2] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const float e = ex[c], d = dxv[c];
+          const float et0 = e * t0[c];
+          v2[0] += ch0[c] + ch1[c];
+          v2[1] += et0;
+          v2[2] = fmaf(d, et0, v2[2]);
+          v2[3] = fmaf(d * d, et0, v2[3]);
+          v2[4] = fmaf(e, t1[c], v2[4]);
+          v2[5] = fmaf(e, t2[c], v2[5]);
+        }
+#pragma unroll
+        for (int k = 0; k < K2; ++k) red[k * RS + lg] = v2[k];
+      }
+      group_reduce<L, K2>(red, tot2, lg, gmask);
+      const float chiu = tot2[0];
+      const float Su = fmaf(-alpha, F, Gs);             // sum u = G' - alpha F
+      float chi = chiu - 2.f * bp * Su + Nf * bp * bp;  // Eq. 2: sum (u - beta')^2
+      if (!okD || !isfinite(alpha)) chi = __int_as_float(0x7fc00000);
+      ++evals;
+
+      // -------------------------------------------------------------- chi^2 change
+      // delta = chi_t^2 - chi_b^2, refined near the two decision thresholds. The window
+      // covers the FP32 error of each chi^2: the rounding of alpha f in every residual
+      // adds at most 2 eps |alpha| sqrt(chi^2 F(bold)) (Cauchy-Schwarz), taken twice here.
+      const float noise = 4.f * 5.9604645e-8f * fabsf(alpha) * sqrtf(fmaxf(chi, 0.f) * FF);
+      float delta = chi - chib;
+      const float win = kTieWindow * chib + noise + noiseb;
+      if (!first_eval && isfinite(chi) && isfinite(chib) && delta >= -a.min_delta * chib - win &&
+          delta <= win) {
+        const float sbx = p[2], sby = iso ? p[2] : p[3];
+        const float ivbx = inv_sq(sbx), ivby = inv_sq(sby);
+        const float nhbx = -0.5f * ivbx, nhby = -0.5f * ivby;
+        const float dsx = sx - sbx, dsy = sy - sby;
+        const float d0 = pe[0] - p[0], d1 = pe[1] - p[1];
+        const float kx = dsx * (sx + sbx) * ivx * ivbx, ky = dsy * (sy + sby) * ivy * ivby;
+        float mx[C], omx[C], exb[C], cab[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int x = lg + L * c;
+          const float db = (float)x - p[0], dt = dxv[c];
+          // exponent difference x_t - x_b, from the parameter differences
+          const float dxe = 0.5f * fmaf(d0 * (dt + db), ivx, db * db * kx);
+          mx[c] = (x < W) ? expm1f(dxe) : 0.f;
+          omx[c] = 1.f + mx[c];
+          exb[c] = (x < W) ? __expf(db * db * nhbx) : 0.f;
+          cab[c] = -alb * exb[c];
+        }
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          const int y = lg + L * k;
+          if (y < R) {
+            const float db = (float)y - p[1], dt = (float)y - pe[1];
+            const float dye = 0.5f * fmaf(d1 * (dt + db), ivy, db * db * ky);
+            rtab[y] = (y < H) ? make_float2(expm1f(dye), __expf(db * db * nhby))
+                              : make_float2(0.f, 0.f);
+          }
+        }
+        __syncwarp(gmask);
+        const float dal = alpha - alb, dbp = bp - bpb;
+        float acc = 0.f;
+#pragma unroll
+        for (int y = 0; y < R; ++y) {
+          if (y < H) {  // padding rows and columns are not part of the spot
+            const float2 q = rtab[y];  // (e_y,t / e_y,b - 1, e_y,b)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              if (lg + L * c < W) {
+                const float fb = exb[c] * q.y;
+                const float tt = fmaf(q.x, omx[c], mx[c]);             // f_t / f_b - 1
+                const float dh = fmaf(fb, fmaf(alpha, tt, dal), dbp);  // h_t - h_b
+                const float rb = fmaf(cab[c], q.y, g[c][y]) - bpb;     // g - h_b
+                acc = fmaf(dh, fmaf(-2.f, rb, dh), acc);
+              }
+            }
+          }
+        }
+        red[lg] = acc;
+        group_reduce<L, 1>(red, tot3, lg, gmask);
+        delta = tot3[0];
+      }
+
+      // -------------------------------------------------------------- LM step
+      const float beta = bp + shift;
+      bool finish = false, need_grad = false, need_solve = false;
+      int state = FS_STATE_MAX_ITER;
+      float ra = alpha, rb = beta, rc = chi;  // values reported on finish
+      if (first_eval) {
+        first_eval = false;
+        it = 1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) p[j] = pe[j];
+        if (isnan(chi)) {
+          finish = true;
+          state = FS_STATE_NOT_CONVERGED;
+        } else if (chi < a.max_error) {
+          finish = true;
+          state = FS_STATE_MAX_ERROR;
+        } else {
+          chib = chi;
+          alb = alpha;
+          bpb = bp;
+          noiseb = noise;
+          need_grad = true;
+        }
+      } else {
+        const float Chi = chi;
+        const bool nan_t = isnan(Chi);
+        if (first_trial && !nan_t && delta < 0.f) --klam;  // error decreased: lambda / 10
+        first_trial = false;
+        const float ms = a.min_step;
+        const bool small = fabsf(dl[0]) < ms * fabsf(p[0]) && fabsf(dl[1]) < ms * fabsf(p[1]) &&
+                           fabsf(dl[2]) < ms * fabsf(p[2]) &&
+                           (iso || fabsf(dl[3]) < ms * fabsf(p[3]));
+        if (!small && !nan_t && delta > 0.f && klam < 4) {
+          ++klam;  // reject: lambda * 10, same normal equations
+          need_solve = true;
+        } else if (nan_t || delta > 0.f) {
+          finish = true;  // keep the best point
+          state = (small && !nan_t) ? FS_STATE_NO_DECREASE : FS_STATE_NOT_CONVERGED;
+          ra = alb;
+          rb = bpb + shift;
+          rc = chib;
+        } else {
+          const float chi_prev = chib;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) p[j] = pe[j];
+          chib = Chi;
+          alb = alpha;
+          bpb = bp;
+          noiseb = noise;
+          if (Chi < a.max_error) {
+            finish = true;
+            state = FS_STATE_MAX_ERROR;
+          } else if (delta > -a.min_delta * chi_prev) {
+            finish = true;
+            state = FS_STATE_MIN_DELTA;
+          } else if (small) {
+            finish = true;
+            state = FS_STATE_MIN_STEP;
+          } else if (it >= a.max_iter) {
+            finish = true;
+            state = FS_STATE_MAX_ITER;
+          } else {
+            ++it;
+            need_grad = true;
+          }
+        }
+      }
+
+      if (need_grad) {
+        // normal equations at p (= pe) from this evaluation's sums
+        const float X11 = tot1[5], X21 = tot1[6], X12 = tot1[7], X22 = tot1[8], X32 = tot1[9],
+                    X42 = tot1[10];
+        const float Y11 = tot1[11], Y21 = tot1[12], Y12 = tot1[13], Y22 = tot1[14],
+                    Y32 = tot1[15], Y42 = tot1[16];
+        const float Tf = tot2[1], Tx = tot2[2], Txx = tot2[3], Ty1 = tot2[4], Ty2 = tot2[5];
+        const float eta = pe[1] - yc0;
+        const float cx = __fdividef(ivx, sx), cy = __fdividef(ivy, sy);
+        const float Sfdy = fmaf(-eta, Tf, Ty1);
+        const float Sfdy2 = Ty2 - 2.f * eta * Ty1 + eta * eta * Tf;
+        float Rd[4], D1[4], Fd[4], aa[4], bb[4];
+        Rd[0] = ivx * fmaf(-bp * X11, Y01, Tx);    // sum r df/dx0     (r = u - beta')
+        Rd[1] = ivy * fmaf(-bp * X01, Y11, Sfdy);  // sum r df/dy0
+        Rd[2] = cx * fmaf(-bp * X21, Y01, Txx);    // sum r df/dsx
+        Rd[3] = cy * fmaf(-bp * X01, Y21, Sfdy2);  // sum r df/dsy
+        D1[0] = X11 * Y01 * ivx;
+        D1[1] = X01 * Y11 * ivy;
+        D1[2] = X21 * Y01 * cx;
+        D1[3] = X01 * Y21 * cy;
+        Fd[0] = X12 * Y02 * ivx;
+        Fd[1] = X02 * Y12 * ivy;
+        Fd[2] = X22 * Y02 * cx;
+        Fd[3] = X02 * Y22 * cy;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          aa[j] = (Nf * Rd[j] - alpha * (Nf * Fd[j] - F * D1[j])) * iD;  // d alpha^/dp_j
+          bb[j] = (alpha * (F * Fd[j] - FF * D1[j]) - F * Rd[j]) * iD;   // d beta^/dp_j
+        }
+        const float a2 = alpha * alpha;
+        float Dd[10];
+        Dd[0] = X22 * Y02 * ivx * ivx;
+        Dd[1] = X12 * Y12 * ivx * ivy;
+        Dd[2] = X32 * Y02 * ivx * cx;
+        Dd[3] = X12 * Y22 * ivx * cy;
+        Dd[4] = X02 * Y22 * ivy * ivy;
+        Dd[5] = X22 * Y12 * ivy * cx;
+        Dd[6] = X02 * Y32 * ivy * cy;
+        Dd[7] = X42 * Y02 * cx * cx;
+        Dd[8] = X22 * Y22 * cx * cy;
+        Dd[9] = X02 * Y42 * cy * cy;
+        float M[10];
+        int idx = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int k = j; k < 4; ++k, ++idx)
+            M[idx] = fmaf(aa[j], Rd[k], alpha * (Fd[j] * aa[k] + D1[j] * bb[k])) + a2 * Dd[idx];
+        if (iso) {  // sigma_x = sigma_y = sigma: fold the two width columns into one
+          A[0] = M[0];
+          A[1] = M[1];
+          A[2] = M[2] + M[3];
+          A[3] = 0.f;
+          A[4] = M[4];
+          A[5] = M[5] + M[6];
+          A[6] = 0.f;
+          A[7] = M[7] + 2.f * M[8] + M[9];
+          A[8] = 0.f;
+          A[9] = 1.f;
+          bv[0] = alpha * Rd[0];
+          bv[1] = alpha * Rd[1];
+          bv[2] = alpha * (Rd[2] + Rd[3]);
+          bv[3] = 0.f;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 10; ++k) A[k] = M[k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) bv[j] = alpha * Rd[j];
+        }
+        first_trial = true;
+        need_solve = true;
+      }
+      if (need_solve) {
+        float d[4];
+        if (solve_damped(A, bv, pow10i(klam), d)) {
+          if (iso) d[3] = d[2];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            dl[j] = d[j];
+            pe[j] = p[j] + d[j];
+          }
+          limit_params(pe, W, H, iso);
+        } else {
+          finish = true;
+          state = FS_STATE_NOT_CONVERGED;
+          ra = alb;
+          rb = bpb + shift;
+          rc = chib;
+        }
+      }
+
+      if (finish) {
+        if (lg == 0) {
+          a.out_params[4 * spot + 0] = p[0];
+          a.out_params[4 * spot + 1] = p[1];
+          a.out_params[4 * spot + 2] = p[2];
+          a.out_params[4 * spot + 3] = iso ? p[2] : p[3];
+          a.out_alpha[spot] = ra;
+          a.out_beta[spot] = rb;
+          a.out_chi2[spot] = rc / (Nf - (float)(P + 2));
+          a.out_state[spot] = state;
+          a.out_iters[spot] = it;
+          if (a.out_evals) a.out_evals[spot] = evals;
+        }
+        active = false;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ configurations
+// id -> (L, C, R); one kernel instantiation each. For every row bound R, the width
+// bound 8 has (4,2) (8,1); 16 has (4,4) (8,2) (16,1); 24 has (8,3); 32 has (8,4) (16,2)
+// (32,1).
+struct CfgDesc {
+  int L, C, R;
+};
+#define FS_CONFIGS_R(X, b, R)                                                                 \
+  X(b + 0, 4, 2, R) X(b + 1, 8, 1, R) X(b + 2, 4, 4, R) X(b + 3, 8, 2, R) X(b + 4, 16, 1, R) \
+  X(b + 5, 8, 3, R) X(b + 6, 8, 4, R) X(b + 7, 16, 2, R) X(b + 8, 32, 1, R)
+#define FS_CONFIGS(X) \
+  FS_CONFIGS_R(X, 0, 8) FS_CONFIGS_R(X, 9, 16) FS_CONFIGS_R(X, 18, 24) FS_CONFIGS_R(X, 27, 32)
+
+#define FS_DESC(id, L, C, R) {L, C, R},
+constexpr CfgDesc kConfigs[] = {FS_CONFIGS(FS_DESC)};
+#undef FS_DESC
+constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
+
+typedef void (*FitKernelFn)(FitArgs, ClassList);
+#define FS_PTR(id, L, C, R) &fit_kernel<L, C, R>,
+const FitKernelFn kKernels[] = {FS_CONFIGS(FS_PTR)};
+#undef FS_PTR
+
+size_t config_smem_bytes(int cfg) {
+  return (size_t)kWarpsPerBlock * warp_smem_floats(kConfigs[cfg].L, kConfigs[cfg].R) * sizeof(float);
+}
+
+// ------------------------------------------------------------------ schedule prepass
+constexpr int kPrepassThreads = 256;
+constexpr int kPrepassChunk = 2048;
+
+__global__ void __launch_bounds__(kPrepassThreads) classify_count_kernel(FitArgs a) {
+  __shared__ int h[kNumClasses];
+  if (threadIdx.x < kNumClasses) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int lo = blockIdx.x * kPrepassChunk;
+  const int hi = min(a.n, lo + kPrepassChunk);
+  for (int s = lo + threadIdx.x; s < hi; s += kPrepassThreads) {
+    int W, H, m;
+    if (spot_valid(a, s, W, H, m)) atomicAdd(&h[size_class(W, H)], 1);
+    else write_invalid(a, s);
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumClasses && h[threadIdx.x]) atomicAdd(&a.counts[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void classify_scan_kernel(FitArgs a) {
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+      a.starts[c] = acc;
+      acc += a.counts[c];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPrepassThreads) classify_scatter_kernel(FitArgs a) {
+  __shared__ int h[kNumClasses], base[kNumClasses];
+  if (threadIdx.x < kNumClasses) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int lo = blockIdx.x * kPrepassChunk;
+  const int hi = min(a.n, lo + kPrepassChunk);
+  for (int s = lo + threadIdx.x; s < hi; s += kPrepassThreads) {
+    int W, H, m;
+    if (spot_valid(a, s, W, H, m)) atomicAdd(&h[size_class(W, H)], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumClasses) {
+    base[threadIdx.x] =
+        h[threadIdx.x] ? a.starts[threadIdx.x] + atomicAdd(&a.fill[threadIdx.x], h[threadIdx.x]) : 0;
+    h[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  for (int s = lo + threadIdx.x; s < hi; s += kPrepassThreads) {
+    int W, H, m;
+    if (spot_valid(a, s, W, H, m)) {
+      const int c = size_class(W, H);
+      a.perm[base[c] + atomicAdd(&h[c], 1)] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host state
+constexpr size_t kSchedHeaderBytes = 4 * kNumClasses * sizeof(int32_t);  // counts starts cursors fill
+
+int8_t g_class_cfg[kNumClasses];
+std::once_flag g_init_once;
+std::mutex g_cfg_mutex;
+thread_local int g_last_cuda_error = 0;
+
+int config_for(int L, int C, int R) {
+  for (int i = 0; i < kNumConfigs; ++i)
+    if (kConfigs[i].L == L && kConfigs[i].C == C && kConfigs[i].R == R) return i;
+  return -1;
+}
+
+// A configuration serves a class when its columns cover the class's width bound exactly
+// (no wider than the next bound) and its rows equal the class's row bound.
+bool config_fits(int cfg, int cls) {
+  if (cfg < 0 || cfg >= kNumConfigs || cls < 0 || cls >= kNumClasses) return false;
+  const int wmax = (cls / 4 + 1) * 8, hmax = (cls % 4 + 1) * 8;
+  const int cols = kConfigs[cfg].L * kConfigs[cfg].C;
+  return cols >= wmax && cols < wmax + 8 && kConfigs[cfg].R == hmax;
+}
+
+void init_defaults() {
+  static const int lc[4][2] = {{8, 1}, {16, 1}, {8, 3}, {32, 1}};  // by width bound 8..32
+  for (int cls = 0; cls < kNumClasses; ++cls) {
+    const int wb = cls / 4, hb = cls % 4;
+    g_class_cfg[cls] = (int8_t)config_for(lc[wb][0], lc[wb][1], (hb + 1) * 8);
+  }
+}
+
+struct ClassTable {
+  int8_t cfg[kNumClasses];    // configuration per size class
+  int8_t order[kNumClasses];  // processing order (largest first)
+};
+
+ClassTable current_table() {
+  std::call_once(g_init_once, init_defaults);
+  ClassTable t;
+  std::lock_guard<std::mutex> lk(g_cfg_mutex);
+  for (int c = 0; c < kNumClasses; ++c) t.cfg[c] = g_class_cfg[c];
+  // largest classes first: order by pixel bound (W bound * H bound), descending
+  int k = 0;
+  for (int area = 32 * 32; area > 0; area -= 64)
+    for (int c = 0; c < kNumClasses; ++c)
+      if (((c / 4 + 1) * 8) * ((c % 4 + 1) * 8) == area) t.order[k++] = (int8_t)c;
+  return t;
+}
+
+// Per device: SM count and, per configuration, resident blocks per SM (lazily filled).
+struct DeviceInfo {
+  int sms = 0;
+  int blocks_per_sm[kNumConfigs] = {};
+};
+DeviceInfo g_dev_info[64];
+std::mutex g_dev_mutex;
+
+int set_cuda_error(cudaError_t e) {
+  g_last_cuda_error = (int)e;
+  return FS_ERR_CUDA;
+}
+
+// Grid size of configuration `cfg` on the current device (one wave of resident blocks).
+int config_grid(int cfg, int *grid) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return FS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  DeviceInfo &d = g_dev_info[dev];
+  if (d.sms == 0) {
+    if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return set_cuda_error(e);
+  }
+  if (d.blocks_per_sm[cfg] == 0) {
+    const size_t smem = config_smem_bytes(cfg);
+    if ((e = cudaFuncSetAttribute(kKernels[cfg], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return set_cuda_error(e);
+    int b = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kKernels[cfg], kWarpsPerBlock * 32,
+                                                           smem)) != cudaSuccess)
+      return set_cuda_error(e);
+    d.blocks_per_sm[cfg] = b < 1 ? 1 : b;
+  }
+  *grid = d.sms * d.blocks_per_sm[cfg];
+  return FS_OK;
+}
+
+int check_common(int dtype, int64_t n, int max_iter, double max_error, double min_delta,
+                 double min_step) {
+  if (n < 0 || n > INT32_MAX) return FS_ERR_SIZE;
+  if (dtype != FS_U16 && dtype != FS_F32) return FS_ERR_DTYPE;
+  if (max_iter < 1 || max_iter > 1000) return FS_ERR_MAX_ITER;
+  if (!(max_error >= 0.0) || !isfinite(max_error) || !(min_delta >= 0.0) || !(min_delta < 1.0) ||
+      !(min_step >= 0.0) || !isfinite(min_step))
+    return FS_ERR_TOL;
+  return FS_OK;
+}
+
+void fill_common(FitArgs &a, const void *images, int dtype, int64_t image_elems,
+                 const float *init, int64_t n, int max_iter, double max_error, double min_delta,
+                 double min_step, float *out_params, float *out_alpha, float *out_beta,
+                 float *out_chi2, int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                 void *workspace) {
+  a.images = images;
+  a.dtype = dtype;
+  a.image_elems = image_elems;
+  a.offsets = nullptr;
+  a.dims = nullptr;
+  a.model = nullptr;
+  a.init = init;
+  a.n = (int32_t)n;
+  a.max_iter = max_iter;
+  a.max_error = (float)max_error;
+  a.min_delta = (float)min_delta;
+  a.min_step = (float)min_step;
+  a.out_params = out_params;
+  a.out_alpha = out_alpha;
+  a.out_beta = out_beta;
+  a.out_chi2 = out_chi2;
+  a.out_state = out_state;
+  a.out_iters = out_iters;
+  a.out_evals = out_evals;
+  a.uniform = 0;
+  a.uw = a.uh = a.umodel = 0;
+  int32_t *ws = static_cast<int32_t *>(workspace);
+  a.counts = ws;
+  a.starts = ws + kNumClasses;
+  a.cursors = ws + 2 * kNumClasses;
+  a.fill = ws + 3 * kNumClasses;
+  a.perm = ws + 4 * kNumClasses;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+size_t fit_spots_workspace(int64_t n) {
+  if (n <= 0) return 0;
+  return kSchedHeaderBytes + (size_t)n * sizeof(int32_t);
+}
+
+size_t fit_spots_uniform_workspace(void) { return kSchedHeaderBytes; }
+
+const char *fit_spots_strerror(int code) {
+  switch (code) {
+    case FS_OK: return "ok";
+    case FS_ERR_NULL: return "a required pointer is NULL";
+    case FS_ERR_SIZE: return "spot count or image size out of range";
+    case FS_ERR_DTYPE: return "unknown pixel type";
+    case FS_ERR_MAX_ITER: return "max_iter outside [1, 1000]";
+    case FS_ERR_TOL: return "tolerance negative, not finite, or min_delta >= 1";
+    case FS_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case FS_ERR_CUDA: return "CUDA error";
+    case FS_ERR_ARG: return "argument out of range";
+    default: return "unknown error code";
+  }
+}
+
+int fit_spots_last_cuda_error(void) { return g_last_cuda_error; }
+
+int fit_spots_num_classes(void) { return kNumClasses; }
+int fit_spots_num_configs(void) { return kNumConfigs; }
+
+int fit_spots_config_info(int config, int *lanes, int *cols, int *rows) {
+  if (config < 0 || config >= kNumConfigs) return FS_ERR_ARG;
+  if (lanes) *lanes = kConfigs[config].L;
+  if (cols) *cols = kConfigs[config].C;
+  if (rows) *rows = kConfigs[config].R;
+  return FS_OK;
+}
+
+int fit_spots_config_fits(int size_class, int config) {
+  return config_fits(config, size_class) ? 1 : 0;
+}
+
+int fit_spots_get_config(int size_class) {
+  if (size_class < 0 || size_class >= kNumClasses) return FS_ERR_ARG;
+  std::call_once(g_init_once, init_defaults);
+  std::lock_guard<std::mutex> lk(g_cfg_mutex);
+  return g_class_cfg[size_class];
+}
+
+int fit_spots_set_config(int size_class, int config) {
+  if (!config_fits(config, size_class)) return FS_ERR_ARG;
+  std::call_once(g_init_once, init_defaults);
+  std::lock_guard<std::mutex> lk(g_cfg_mutex);
+  g_class_cfg[size_class] = (int8_t)config;
+  return FS_OK;
+}
+
+int fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
+              const int32_t *roi_dims, const float *init_params, const uint8_t *model, int64_t n,
+              int max_iter, double max_error, double min_delta, double min_step,
+              float *out_params, float *out_alpha, float *out_beta, float *out_chi2,
+              int32_t *out_state, int32_t *out_iters, int32_t *out_evals, void *workspace,
+              size_t ws_bytes, void *stream) {
+  int rc = check_common(dtype, n, max_iter, max_error, min_delta, min_step);
+  if (rc) return rc;
+  if (image_elems < 0) return FS_ERR_SIZE;
+  if (n == 0) return FS_OK;
+  if (!images || !offsets || !roi_dims || !init_params || !model || !out_params || !out_alpha ||
+      !out_beta || !out_chi2 || !out_state || !out_iters || !workspace)
+    return FS_ERR_NULL;
+  if (ws_bytes < fit_spots_workspace(n) || (reinterpret_cast<uintptr_t>(workspace) & 15))
+    return FS_ERR_WORKSPACE;
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FitArgs a;
+  fill_common(a, images, dtype, image_elems, init_params, n, max_iter, max_error, min_delta,
+              min_step, out_params, out_alpha, out_beta, out_chi2, out_state, out_iters, out_evals,
+              workspace);
+  a.offsets = offsets;
+  a.dims = roi_dims;
+  a.model = model;
+
+  cudaError_t e = cudaMemsetAsync(workspace, 0, kSchedHeaderBytes, st);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  const int pblocks = (int)((n + kPrepassChunk - 1) / kPrepassChunk);
+  classify_count_kernel<<<pblocks, kPrepassThreads, 0, st>>>(a);
+  classify_scan_kernel<<<1, 32, 0, st>>>(a);
+  classify_scatter_kernel<<<pblocks, kPrepassThreads, 0, st>>>(a);
+  // one persistent launch per configuration in use, covering all of its classes,
+  // configurations in the order of their largest class
+  const ClassTable ct = current_table();
+  bool done[kNumConfigs] = {};
+  for (int oi = 0; oi < kNumClasses; ++oi) {
+    const int cfg = ct.cfg[ct.order[oi]];
+    if (cfg < 0 || cfg >= kNumConfigs || done[cfg]) continue;
+    done[cfg] = true;
+    ClassList cl;
+    cl.count = 0;
+    for (int oj = oi; oj < kNumClasses; ++oj)
+      if (ct.cfg[ct.order[oj]] == cfg) cl.cls[cl.count++] = ct.order[oj];
+    int grid = 0;
+    rc = config_grid(cfg, &grid);
+    if (rc) return rc;
+    kKernels[cfg]<<<grid, kWarpsPerBlock * 32, config_smem_bytes(cfg), st>>>(a, cl);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_cuda_error(e);
+  return FS_OK;
+}
+
+int fit_spots_uniform(const void *images, int dtype, int width, int height, int model_id,
+                      const float *init_params, int64_t n, int max_iter, double max_error,
+                      double min_delta, double min_step, float *out_params, float *out_alpha,
+                      float *out_beta, float *out_chi2, int32_t *out_state, int32_t *out_iters,
+                      int32_t *out_evals, void *workspace, size_t ws_bytes, void *stream) {
+  int rc = check_common(dtype, n, max_iter, max_error, min_delta, min_step);
+  if (rc) return rc;
+  const int P = model_id == FS_MODEL_ISO ? 3 : 4;
+  if ((model_id != FS_MODEL_ISO && model_id != FS_MODEL_ELLIPTIC) || width < 3 || height < 3 ||
+      width > kMaxSide || height > kMaxSide || width * height <= P + 2)
+    return FS_ERR_ARG;
+  if (n == 0) return FS_OK;
+  if (!images || !init_params || !out_params || !out_alpha || !out_beta || !out_chi2 ||
+      !out_state || !out_iters || !workspace)
+    return FS_ERR_NULL;
+  if (ws_bytes < fit_spots_uniform_workspace() || (reinterpret_cast<uintptr_t>(workspace) & 15))
+    return FS_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FitArgs a;
+  fill_common(a, images, dtype, n * width * height, init_params, n, max_iter, max_error,
+              min_delta, min_step, out_params, out_alpha, out_beta, out_chi2, out_state,
+              out_iters, out_evals, workspace);
+  a.uniform = 1;
+  a.uw = width;
+  a.uh = height;
+  a.umodel = model_id;
+  a.perm = nullptr;
+  const int cls = ((width + 7) / 8 - 1) * 4 + ((height + 7) / 8 - 1);
+  const ClassTable ct = current_table();
+  const int cfg = ct.cfg[cls];
+  ClassList cl;
+  cl.count = 1;
+  cl.cls[0] = (int8_t)cls;
+  int grid = 0;
+  rc = config_grid(cfg, &grid);
+  if (rc) return rc;
+  cudaError_t e = cudaMemsetAsync(workspace, 0, kSchedHeaderBytes, st);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  kKernels[cfg]<<<grid, kWarpsPerBlock * 32, config_smem_bytes(cfg), st>>>(a, cl);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_cuda_error(e);
+  return FS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+"""Thin Python binding of ``include/fitspots.h`` (ctypes; argument marshalling only).
+
+Every step of the fit runs in the CUDA library ``_build/libfitspots.so``. PyTorch only
+provides device memory and the stream. There is no CPU fallback: if the library is not
+built, or a tensor is not on a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import torch
+
+from .build import LIB
+
+MODEL_ISO, MODEL_ELLIPTIC = 0, 1
+U16, F32 = 0, 1
+STATE = {"MAX_ITER": 0, "MIN_DELTA": 1, "MIN_STEP": 2, "MAX_ERROR": 3, "NO_DECREASE": 4,
+         "NOT_CONVERGED": -1, "INVALID_ROI": -2}
+CONVERGED_STATES = (1, 2, 3, 4)
+
+
+class FitSpotsError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not Path(LIB).exists():
+            raise FitSpotsError(f"{LIB} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(str(LIB))
+        vp, i, i64, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        lib.fit_spots.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
+                                  vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        lib.fit_spots.restype = i
+        lib.fit_spots_uniform.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
+                                          vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        lib.fit_spots_uniform.restype = i
+        lib.fit_spots_uniform_workspace.argtypes = []
+        lib.fit_spots_uniform_workspace.restype = sz
+        lib.fit_spots_config_fits.argtypes = [i, i]
+        lib.fit_spots_config_fits.restype = i
+        lib.fit_spots_workspace.argtypes = [i64]
+        lib.fit_spots_workspace.restype = sz
+        lib.fit_spots_strerror.argtypes = [i]
+        lib.fit_spots_strerror.restype = ctypes.c_char_p
+        lib.fit_spots_last_cuda_error.argtypes = []
+        lib.fit_spots_last_cuda_error.restype = i
+        lib.fit_spots_num_classes.restype = i
+        lib.fit_spots_num_configs.restype = i
+        lib.fit_spots_config_info.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.fit_spots_config_info.restype = i
+        lib.fit_spots_get_config.argtypes = [i]
+        lib.fit_spots_get_config.restype = i
+        lib.fit_spots_set_config.argtypes = [i, i]
+        lib.fit_spots_set_config.restype = i
+        _lib = lib
+    return _lib
+
+
+def check(rc: int, what: str = "fit_spots") -> None:
+    if rc != 0:
+        lib = library()
+        msg = lib.fit_spots_strerror(rc).decode()
+        if rc == -7:
+            msg += f" (cudaError {lib.fit_spots_last_cuda_error()})"
+        raise FitSpotsError(f"{what} failed: {msg} [{rc}]")
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t: torch.Tensor, dtype, name: str, device) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise FitSpotsError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise FitSpotsError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise FitSpotsError(f"{name} is on {t.device}, expected {device}")
+    if not t.is_contiguous():
+        raise FitSpotsError(f"{name} must be contiguous")
+    return t
+
+
+def workspace_bytes(n: int) -> int:
+    return int(library().fit_spots_workspace(int(n)))
+
+
+def alloc_outputs(n: int, device) -> dict:
+    return dict(params=torch.empty((n, 4), dtype=torch.float32, device=device),
+                alpha=torch.empty(n, dtype=torch.float32, device=device),
+                beta=torch.empty(n, dtype=torch.float32, device=device),
+                chi2=torch.empty(n, dtype=torch.float32, device=device),
+                state=torch.empty(n, dtype=torch.int32, device=device),
+                iters=torch.empty(n, dtype=torch.int32, device=device),
+                evals=torch.empty(n, dtype=torch.int32, device=device))
+
+
+def fit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor, init: torch.Tensor,
+        model: torch.Tensor, *, max_iter: int = 20, max_error: float = 0.0,
+        min_delta: float = 1e-6, min_step: float = 1e-4, out: dict | None = None,
+        workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None) -> dict:
+    """Fit all spots; returns (or fills ``out``) params [n,4], alpha, beta, chi2 (normalised),
+    state, iters, evals. Asynchronous on ``stream`` (default: the current stream)."""
+    dev = images.device
+    if dev.type != "cuda":
+        raise FitSpotsError("images must be a CUDA tensor")
+    if images.dtype == torch.uint16:
+        dtype = U16
+    elif images.dtype == torch.float32:
+        dtype = F32
+    else:
+        raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
+    _need(images, images.dtype, "images", dev)
+    n = int(offsets.numel())
+    _need(offsets, torch.int64, "offsets", dev)
+    _need(dims, torch.int32, "dims", dev)
+    _need(init, torch.float32, "init", dev)
+    _need(model, torch.uint8, "model", dev)
+    if dims.numel() != 2 * n or init.numel() != 4 * n or model.numel() != n:
+        raise FitSpotsError("offsets, dims, init and model disagree on the spot count")
+    o = out if out is not None else alloc_outputs(n, dev)
+    ws_need = workspace_bytes(n)
+    if workspace is None:
+        workspace = torch.empty(max(ws_need, 16), dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = library().fit_spots(
+            _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(init), _ptr(model),
+            n, int(max_iter), float(max_error), float(min_delta), float(min_step),
+            _ptr(o["params"]), _ptr(o["alpha"]), _ptr(o["beta"]), _ptr(o["chi2"]), _ptr(o["state"]),
+            _ptr(o["iters"]), _ptr(o.get("evals")), _ptr(workspace), workspace.numel(),
+            ctypes.c_void_p(s.cuda_stream))
+    check(rc)
+    return o
+
+
+def fit_uniform(images: torch.Tensor, width: int, height: int, model: int, init: torch.Tensor, *,
+                max_iter: int = 20, max_error: float = 0.0, min_delta: float = 1e-6,
+                min_step: float = 1e-4, out: dict | None = None,
+                workspace: torch.Tensor | None = None,
+                stream: torch.cuda.Stream | None = None) -> dict:
+    """Fit n spots of one size and model stored back to back (spot s at s*W*H)."""
+    dev = images.device
+    if dev.type != "cuda":
+        raise FitSpotsError("images must be a CUDA tensor")
+    if images.dtype == torch.uint16:
+        dtype = U16
+    elif images.dtype == torch.float32:
+        dtype = F32
+    else:
+        raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
+    _need(images, images.dtype, "images", dev)
+    _need(init, torch.float32, "init", dev)
+    n = init.numel() // 4
+    if init.numel() != 4 * n or images.numel() < n * width * height:
+        raise FitSpotsError("init must be [n, 4] and images must hold n*W*H elements")
+    o = out if out is not None else alloc_outputs(n, dev)
+    if workspace is None:
+        workspace = torch.empty(max(int(library().fit_spots_uniform_workspace()), 16),
+                                dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = library().fit_spots_uniform(
+            _ptr(images), dtype, int(width), int(height), int(model), _ptr(init), n,
+            int(max_iter), float(max_error), float(min_delta), float(min_step),
+            _ptr(o["params"]), _ptr(o["alpha"]), _ptr(o["beta"]), _ptr(o["chi2"]), _ptr(o["state"]),
+            _ptr(o["iters"]), _ptr(o.get("evals")), _ptr(workspace), workspace.numel(),
+            ctypes.c_void_p(s.cuda_stream))
+    check(rc, "fit_spots_uniform")
+    return o
+
+
+def fit_batch(batch, **kw) -> dict:
+    """``fit`` on a :class:`synth.SpotBatch` living on a CUDA device."""
+    return fit(batch.images, batch.offsets, batch.dims, batch.init, batch.model, **kw)
+
+
+def configs() -> list[tuple[int, int, int]]:
+    lib = library()
+    out = []
+    for c in range(lib.fit_spots_num_configs()):
+        L, C, R = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib.fit_spots_config_info(c, ctypes.byref(L), ctypes.byref(C), ctypes.byref(R)),
+              "fit_spots_config_info")
+        out.append((L.value, C.value, R.value))
+    return out
+
+
+def get_config(size_class: int) -> int:
+    return int(library().fit_spots_get_config(int(size_class)))
+
+
+def config_fits(size_class: int, config: int) -> bool:
+    return bool(library().fit_spots_config_fits(int(size_class), int(config)))
+
+
+def set_config(size_class: int, config: int) -> None:
+    check(library().fit_spots_set_config(int(size_class), int(config)), "fit_spots_set_config")

@@ -69,6 +69,17 @@ class SpotBatch:
                     dims=self.dims.cpu().numpy(), model=self.model.cpu().numpy(),
                     init=self.init.cpu().numpy())
 
+    def head(self, n: int) -> "SpotBatch":
+        """The first n spots, sharing storage (spots are packed in index order)."""
+        n = int(n)
+        if n == 0:
+            end = 0
+        else:
+            last = n - 1
+            end = int(self.offsets[last].item() + self.dims[last, 0].item() * self.dims[last, 1].item())
+        return SpotBatch(self.images[:end], self.offsets[:n], self.dims[:n], self.model[:n],
+                         self.init[:n], {k: v[:n] for k, v in self.truth.items()}, self.name)
+
     def subset(self, idx) -> "SpotBatch":
         """Spots ``idx`` repacked densely (each keeps its own padding rule)."""
         idx = torch.as_tensor(idx, dtype=torch.int64, device=self.offsets.device)

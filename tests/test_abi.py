@@ -1,0 +1,120 @@
+"""The C-ABI library builds, loads and exports every declared symbol; host-side argument
+checks reject bad calls before any GPU work (no GPU needed)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_02045_gb300 import build, fitspots
+    build.build()
+    return fitspots.library()
+
+
+def _declared():
+    names = []
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([A-Za-z_]\w*)\s*\(", text, flags=re.M):
+            if m.group(1) not in ("defined",):
+                names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = _declared()
+    assert "fit_spots" in names and "fit_spots_uniform" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_workspace_sizes(lib):
+    assert lib.fit_spots_workspace(0) == 0
+    assert lib.fit_spots_workspace(-5) == 0
+    assert lib.fit_spots_workspace(1000) == 256 + 4 * 1000
+    assert lib.fit_spots_uniform_workspace() == 256
+
+
+def _call(lib, **over):
+    """fit_spots with dummy (never dereferenced) pointers; only argument checks run."""
+    fake = ctypes.c_void_p(0x1000)
+    a = dict(images=fake, dtype=1, image_elems=100, offsets=fake, dims=fake, init=fake,
+             model=fake, n=10, max_iter=20, max_error=0.0, min_delta=1e-6, min_step=1e-4,
+             params=fake, alpha=fake, beta=fake, chi2=fake, state=fake, iters=fake,
+             evals=None, ws=fake, ws_bytes=0, stream=None)
+    a.update(over)
+    return lib.fit_spots(a["images"], a["dtype"], a["image_elems"], a["offsets"], a["dims"],
+                         a["init"], a["model"], a["n"], a["max_iter"], a["max_error"],
+                         a["min_delta"], a["min_step"], a["params"], a["alpha"], a["beta"],
+                         a["chi2"], a["state"], a["iters"], a["evals"], a["ws"], a["ws_bytes"],
+                         a["stream"])
+
+
+def test_argument_checks(lib):
+    assert _call(lib, n=0) == 0                       # nothing to do, nothing enqueued
+    assert _call(lib, n=-1) == -2
+    assert _call(lib, n=2**31) == -2
+    assert _call(lib, image_elems=-1) == -2
+    assert _call(lib, dtype=7) == -3
+    assert _call(lib, max_iter=0) == -4
+    assert _call(lib, max_iter=1001) == -4
+    assert _call(lib, min_delta=-1e-6) == -5
+    assert _call(lib, min_delta=1.0) == -5
+    assert _call(lib, min_step=float("nan")) == -5
+    assert _call(lib, max_error=float("inf")) == -5
+    assert _call(lib, images=None) == -1
+    assert _call(lib, ws=None) == -1
+    assert _call(lib, ws_bytes=10) == -6                # smaller than fit_spots_workspace(10)
+    assert _call(lib, ws=ctypes.c_void_p(0x1004), ws_bytes=1 << 20) == -6   # misaligned
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert lib.fit_spots_strerror(code)
+    assert lib.fit_spots_last_cuda_error() == 0
+
+
+def test_uniform_argument_checks(lib):
+    fake = ctypes.c_void_p(0x1000)
+
+    def call(W=32, H=32, model=1, n=10, ws=fake, ws_bytes=256, max_iter=20):
+        return lib.fit_spots_uniform(fake, 0, W, H, model, fake, n, max_iter, 0.0, 1e-6, 1e-4,
+                                     fake, fake, fake, fake, fake, fake, None, ws, ws_bytes, None)
+    assert call(W=2) == -8 and call(H=33) == -8 and call(model=3) == -8
+    assert call(n=0) == 0
+    assert call(ws_bytes=16) == -6
+    assert call(ws=None) == -1
+    assert call(max_iter=0) == -4
+
+
+def test_size_classes_and_configs(lib):
+    from paper_2106_02045_gb300 import fitspots
+    assert lib.fit_spots_num_classes() == 16
+    cfgs = fitspots.configs()
+    assert len(cfgs) == lib.fit_spots_num_configs() == 36
+    for cls in range(16):
+        wmax, hmax = (cls // 4 + 1) * 8, (cls % 4 + 1) * 8
+        usable = [c for c in range(len(cfgs)) if fitspots.config_fits(cls, c)]
+        assert usable, cls
+        for c in usable:
+            L, C, R = cfgs[c]
+            assert L * C >= wmax and L * C < wmax + 8 and R == hmax and 32 % L == 0
+        assert fitspots.get_config(cls) in usable
+    assert lib.fit_spots_set_config(15, 0) == -8          # (4,2,8) cannot hold 32x32
+    keep = fitspots.get_config(15)
+    other = [c for c in range(len(cfgs)) if fitspots.config_fits(15, c) and c != keep][0]
+    fitspots.set_config(15, other)
+    assert fitspots.get_config(15) == other
+    fitspots.set_config(15, keep)
+    assert lib.fit_spots_get_config(16) == -8 and lib.fit_spots_config_info(99, None, None, None) == -8
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    from paper_2106_02045_gb300 import fitspots
+    x = torch.zeros(100)
+    with pytest.raises(fitspots.FitSpotsError):
+        fitspots.fit(x, torch.zeros(1, dtype=torch.int64), torch.zeros(1, 2, dtype=torch.int32),
+                     torch.zeros(1, 4), torch.zeros(1, dtype=torch.uint8))

@@ -1,0 +1,186 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded synthetic workloads.
+
+The bar (per spot): centre within 1e-3 px, sigma, alpha and beta within 1e-4 relative,
+and the same convergence class (converged = MIN_DELTA, MIN_STEP, MAX_ERROR, NO_DECREASE).
+It is asserted on determined spots: the FP64 fit converged to a positive amplitude above
+the noise, no parameter is held at the limit() box, and its own normal matrix gives a
+centre standard error <= 0.1 px and a width standard error <= 10 %. All-spot agreement is
+asserted at a looser level because on a flat chi^2 surface (dim spots, widths running to
+the box) the min_delta stop leaves end points that move with rounding in any two
+implementations.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2106_02045_gb300 import fitspots, synth
+from tests.parity import compare, determined, run_oracle, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _fit(batch, **kw):
+    g = batch.to(DEV)
+    out = fitspots.fit_batch(g, **kw)
+    torch.cuda.synchronize()
+    return to_numpy(out)
+
+
+def _report(name, m):
+    print(f"{name}: n={m['n']} class {m['class_agree']:.5f} bar(conv) {m['bar_converged']:.5f} "
+          f"determined {m['n_well_posed']} class {m['class_agree_wp']:.5f} bar {m['bar_wp']:.5f} "
+          f"max|dxy| {m['max_dxy_wp']:.2e}")
+
+
+@pytest.mark.parametrize("name,n,all_class,all_bar", [
+    ("iso15", 10_000, 0.999, 0.995),
+    ("iso16", 20_000, 0.999, 0.995),
+    ("ell32", 20_000, 0.995, 0.97),
+    ("mixed", 20_000, 0.995, 0.97),
+])
+def test_parity_against_oracle(name, n, all_class, all_bar):
+    b = synth.make_workload(name, n)
+    out = _fit(b)
+    ref = run_oracle(b)
+    m = compare(out, ref, b.dims.numpy(), determined(b, ref))
+    _report(name, m)
+    assert m["n_well_posed"] >= 0.25 * n
+    assert m["class_agree_wp"] >= 0.999
+    assert m["bar_wp"] >= 0.999
+    assert m["class_agree"] >= all_class
+    assert m["bar_converged"] >= all_bar
+
+
+def test_full_size_ell32_sampled():
+    """The 1,000,000-spot 32x32 uint16 workload in the launch the benchmark times, checked
+    on a random sample of spots the oracle fits one by one."""
+    b = synth.make_workload("ell32", None, device=DEV)
+    out = fitspots.fit_uniform(b.images, 32, 32, synth.MODEL_ELLIPTIC, b.init)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(b.n, 4000, replace=False))
+    sub = b.subset(idx).to("cpu")
+    ref = run_oracle(sub)
+    o = {k: v[torch.as_tensor(idx, device=DEV)].cpu().numpy() for k, v in out.items()}
+    m = compare(o, ref, sub.dims.numpy(), determined(sub, ref))
+    _report("ell32-full-sample", m)
+    assert m["class_agree_wp"] >= 0.999 and m["bar_wp"] >= 0.999
+    assert m["class_agree"] >= 0.995
+    conv = np.isin(out["state"].cpu().numpy(), (1, 2, 3, 4))
+    assert conv.mean() > 0.9
+
+
+def test_uniform_and_general_entry_points_agree_bitwise():
+    for name in ("iso15", "ell32"):
+        b = synth.make_workload(name, 3000, device=DEV)
+        o1 = fitspots.fit_batch(b)
+        W, H = int(b.dims[0, 0]), int(b.dims[0, 1])
+        o2 = fitspots.fit_uniform(b.images, W, H, int(b.model[0]), b.init)
+        torch.cuda.synchronize()
+        for k in o1:
+            assert torch.equal(o1[k].view(torch.int32), o2[k].view(torch.int32)), (name, k)
+
+
+def test_deterministic_and_independent_of_batch():
+    b = synth.make_workload("mixed", 6000, device=DEV)
+    o1 = fitspots.fit_batch(b)
+    o2 = fitspots.fit_batch(b)
+    idx = torch.arange(0, 6000, 7, device=DEV)
+    sub = b.subset(idx)
+    o3 = fitspots.fit_batch(sub)
+    torch.cuda.synchronize()
+    for k in o1:
+        assert torch.equal(o1[k].view(torch.int32), o2[k].view(torch.int32)), k
+        assert torch.equal(o1[k][idx].view(torch.int32), o3[k].view(torch.int32)), k
+
+
+def test_noise_free_spots_are_recovered():
+    """Noise-free float32 spots: the fit lands on the truth to float32 accuracy."""
+    rng = np.random.default_rng(11)
+    spots, dims, init, truth, models = [], [], [], [], []
+    for s in range(600):
+        m = s % 2
+        W, H = int(rng.integers(7, 33)), int(rng.integers(7, 33))
+        p = np.array([(W - 1) / 2 + rng.uniform(-1, 1), (H - 1) / 2 + rng.uniform(-1, 1),
+                      rng.uniform(1.0, min(W, H) / 4), rng.uniform(1.0, min(W, H) / 4)])
+        if m == 0:
+            p[3] = p[2]
+        x, y = np.arange(W)[None, :], np.arange(H)[:, None]
+        f = np.exp(-0.5 * ((x - p[0]) / p[2]) ** 2 - 0.5 * ((y - p[1]) / p[3]) ** 2)
+        spots.append((2000.0 * f + 100.0).astype(np.float32).ravel())
+        dims.append((W, H))
+        q = p + np.array([0.4, -0.3, 0.2, 0.15 if m else 0.2])
+        init.append(q)
+        truth.append(p)
+        models.append(m)
+    span = [(len(s) + 3) // 4 * 4 for s in spots]
+    offs = np.cumsum([0] + span[:-1])
+    img = np.zeros(sum(span), np.float32)
+    for o, s in zip(offs, spots):
+        img[o:o + len(s)] = s
+    out = fitspots.fit(torch.from_numpy(img).to(DEV), torch.from_numpy(offs.astype(np.int64)).to(DEV),
+                       torch.tensor(dims, dtype=torch.int32, device=DEV),
+                       torch.tensor(np.array(init), dtype=torch.float32, device=DEV),
+                       torch.tensor(models, dtype=torch.uint8, device=DEV),
+                       max_iter=100, min_delta=0.0, min_step=1e-7)
+    torch.cuda.synchronize()
+    P = out["params"].cpu().numpy()
+    err = np.abs(P - np.array(truth)).max(1)
+    assert np.isin(out["state"].cpu().numpy(), (1, 2, 3, 4)).all()
+    assert err.max() < 2e-3, err.max()
+    assert np.median(err) < 1e-4
+
+
+def test_edge_cases():
+    """Empty batch, invalid ROIs, NaN pixels, max_error, a one-iteration budget, 3x3 ROIs."""
+    b = synth.make_workload("iso15", 64, device=DEV)
+    empty = fitspots.fit(b.images, b.offsets[:0], b.dims[:0], b.init[:0], b.model[:0])
+    assert empty["state"].numel() == 0
+    # invalid spots: too small, too large, bad model, offset past the end
+    dims = b.dims.clone()
+    model = b.model.clone()
+    offs = b.offsets.clone()
+    dims[0] = torch.tensor([2, 15])
+    dims[1] = torch.tensor([33, 15])
+    model[2] = 9
+    offs[3] = b.images.numel() - 10
+    imgs = b.images.clone()
+    imgs[offs[4] + 17] = float("nan")
+    out = fitspots.fit(imgs, offs, dims, b.init, model)
+    torch.cuda.synchronize()
+    st = out["state"].cpu().numpy()
+    assert list(st[:4]) == [-2, -2, -2, -2]
+    assert torch.equal(out["params"][:4], b.init[:4])
+    assert torch.isnan(out["alpha"][:4]).all() and (out["iters"][:4] == 0).all()
+    assert st[4] == -1                                   # NaN pixel -> NOT_CONVERGED
+    assert np.isin(st[5:], (1, 2, 3, 4)).all()
+    # max_error: every spot stops at once with MAX_ERROR
+    out = fitspots.fit_batch(b, max_error=1e30)
+    assert (out["state"] == 3).all() and (out["iters"] == 1).all()
+    # a one-iteration budget: MAX_ITER unless converged in the first step
+    out = fitspots.fit_batch(b, max_iter=1)
+    assert (out["iters"] == 1).all()
+    assert (out["state"] == 0).float().mean() > 0.9
+    ref = run_oracle(b.to("cpu"), max_iter=1)
+    assert np.mean((out["state"].cpu().numpy() == 0) == (ref["state"] == 0)) >= 0.95
+    # 3x3 and 3x5 ROIs of both models
+    small = synth.make_iso(50, 5, 2.0, 99, "cpu")
+    for (W, H, m) in ((3, 3, 0), (3, 5, 1), (5, 3, 1)):
+        n = 20
+        img = torch.full((n * W * H,), 100.0)
+        img[(W * H) // 2::W * H] = 1000.0
+        o = fitspots.fit(img.to(DEV), (torch.arange(n) * W * H).to(DEV),
+                         torch.tensor([[W, H]] * n, dtype=torch.int32, device=DEV),
+                         torch.tensor([[(W - 1) / 2, (H - 1) / 2, 0.8, 0.8]] * n, device=DEV),
+                         torch.full((n,), m, dtype=torch.uint8, device=DEV))
+        torch.cuda.synchronize()
+        assert (o["state"] != -2).all()
+    del small

@@ -123,6 +123,33 @@ int fit_spots_uniform(const void *images, int dtype, int width, int height, int 
                       float *out_beta, float *out_chi2, int32_t *out_state, int32_t *out_iters,
                       int32_t *out_evals, void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * fit_spots without a caller-provided workspace, for callers that cannot allocate device
+ * memory: code that runs where cudaMalloc is unavailable or forbidden (inside a region
+ * being captured into a CUDA graph, a real-time loop with a no-allocation rule, a plugin
+ * whose host application owns every allocation) or that has no allocator of its own at
+ * hand. The paper has no counterpart; this is a convenience of the library.
+ * The schedule scratch is a fixed array compiled into the library, sized for
+ * fit_spots_noalloc_max_spots() = 1,048,576 spots (4 MiB + 256 B), which every GPU that
+ * loads the library holds until the process exits. n above that limit returns
+ * FS_ERR_SIZE. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call before any
+ * stream capture. The call itself allocates nothing and frees nothing. Every call shares
+ * the one array and leaves its schedule in it: calls that may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. Each call
+ * clears the parts that must start at zero, so results never depend on an earlier call.
+ * Arguments and results are those of fit_spots, without workspace and ws_bytes.
+ */
+int fit_spots_noalloc(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
+                      const int32_t *roi_dims, const float *init_params, const uint8_t *model,
+                      int64_t n, int max_iter, double max_error, double min_delta,
+                      double min_step, float *out_params, float *out_alpha, float *out_beta,
+                      float *out_chi2, int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                      void *stream);
+
+/* Largest n fit_spots_noalloc accepts. */
+int64_t fit_spots_noalloc_max_spots(void);
+
 /* Message for an FS_ERR_* / FS_OK code (static storage). */
 const char *fit_spots_strerror(int code);
 

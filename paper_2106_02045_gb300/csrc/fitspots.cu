@@ -957,6 +957,36 @@ void fill_common(FitArgs &a, const void *images, int dtype, int64_t image_elems,
   a.perm = ws + 4 * kNumClasses;
 }
 
+// ------------------------------------------------------------------ built-in scratch
+// Schedule scratch for fit_spots_noalloc: the same layout fit_spots keeps in the caller's
+// workspace (class counts, starts, cursors, scatter cursors, then the spot permutation),
+// sized for kStaticMaxSpots spots. It lives in every GPU that loads the library until the
+// process exits. Host code must not pass g_static_ws itself to a kernel (on the host it
+// names a stand-in, not device memory); its device address is looked up once per device.
+constexpr int64_t kStaticMaxSpots = 1 << 20;
+constexpr size_t kStaticWsBytes = kSchedHeaderBytes + (size_t)kStaticMaxSpots * sizeof(int32_t);
+static __device__ __align__(256) int32_t g_static_ws[kStaticWsBytes / sizeof(int32_t)];
+
+void *g_static_ws_addr[64];
+std::mutex g_static_mutex;
+
+// Device address of g_static_ws on the current device (first use: cudaGetSymbolAddress).
+int static_workspace(void **ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return FS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_static_mutex);
+  if (!g_static_ws_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e != cudaSuccess || !p) return set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    g_static_ws_addr[dev] = p;
+  }
+  *ptr = g_static_ws_addr[dev];
+  return FS_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1111,6 +1141,28 @@ int fit_spots_uniform(const void *images, int dtype, int width, int height, int 
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_cuda_error(e);
   return FS_OK;
+}
+
+int64_t fit_spots_noalloc_max_spots(void) { return kStaticMaxSpots; }
+
+int fit_spots_noalloc(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
+                      const int32_t *roi_dims, const float *init_params, const uint8_t *model,
+                      int64_t n, int max_iter, double max_error, double min_delta,
+                      double min_step, float *out_params, float *out_alpha, float *out_beta,
+                      float *out_chi2, int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                      void *stream) {
+  int rc = check_common(dtype, n, max_iter, max_error, min_delta, min_step);
+  if (rc) return rc;
+  if (n > kStaticMaxSpots) return FS_ERR_SIZE;
+  if (n == 0) return FS_OK;
+  void *ws = nullptr;
+  rc = static_workspace(&ws);
+  if (rc) return rc;
+  // fit_spots clears the schedule header on the stream before use; the permutation is
+  // rewritten in full by the prepass, so nothing from an earlier call leaks through.
+  return fit_spots(images, dtype, image_elems, offsets, roi_dims, init_params, model, n,
+                   max_iter, max_error, min_delta, min_step, out_params, out_alpha, out_beta,
+                   out_chi2, out_state, out_iters, out_evals, ws, kStaticWsBytes, stream);
 }
 
 }  // extern "C"

@@ -150,6 +150,31 @@ int fit_spots_noalloc(const void *images, int dtype, int64_t image_elems, const 
 /* Largest n fit_spots_noalloc accepts. */
 int64_t fit_spots_noalloc_max_spots(void);
 
+/*
+ * Backward pass: vector-Jacobian product of the fitted outputs with respect to the
+ * pixels, by the implicit-function theorem at the minimum of Eq. 2 over (p, alpha,
+ * beta). With K_i = (alpha df_i/dp, f_i, 1), r = g - h and
+ *   M = sum_i K_i K_i^T - sum_i r_i d^2 h_i/d(p, alpha, beta)^2,
+ * grad_images_i = (M^-1 u) . K_i + u_chi2 * 2 r_i / (W*H - P - 2), where u is the
+ * upstream gradient of (params, alpha, beta) (for the isotropic model params[2] and
+ * params[3] both carry sigma, so both upstream slots count) and u_chi2 that of out_chi2.
+ * The start parameters do not move the minimum: their gradient is zero (not written).
+ *   images, dtype, image_elems, offsets, roi_dims, model, n   as passed to fit_spots
+ *   params, alpha, beta, state                                the fit_spots outputs
+ *   grad_params [n][4], grad_alpha [n], grad_beta [n], grad_chi2 [n]   upstream (device;
+ *                                                             any may be NULL = zero)
+ *   grad_images  device float32 buffer of image_elems elements; the pixels of every valid
+ *                spot are written (zeros for spots whose state is not a converged one
+ *                or whose system M is singular); other elements are left untouched.
+ * Not in the paper (the paper has no derivatives of the fit results); derived from Eq. 2.
+ */
+int fit_spots_backward(const void *images, int dtype, int64_t image_elems,
+                       const int64_t *offsets, const int32_t *roi_dims, const uint8_t *model,
+                       int64_t n, const float *params, const float *alpha, const float *beta,
+                       const int32_t *state, const float *grad_params, const float *grad_alpha,
+                       const float *grad_beta, const float *grad_chi2, float *grad_images,
+                       void *stream);
+
 /* Message for an FS_ERR_* / FS_OK code (static storage). */
 const char *fit_spots_strerror(int code);
 

@@ -61,6 +61,10 @@ def _load():
         lib.or_solve_damped.restype = i
         lib.or_limit.argtypes = [i, i, i, vp]
         lib.or_limit.restype = None
+        lib.or_profile_second.argtypes = [i, i, i, vp, vp]
+        lib.or_profile_second.restype = None
+        lib.or_backward.argtypes = [i, i, i, vp, vp, d, d, vp, vp]
+        lib.or_backward.restype = i
         _lib = lib
     return _lib
 
@@ -179,4 +183,25 @@ def fit_spots(images: np.ndarray, offsets, dims, init, model, *, max_iter: int =
                      _p(tr) if tr is not None else None, int(nthreads))
     if trace:
         out["trace"] = tr
+    return out
+
+
+def profile_second(model: int, W: int, H: int, p):
+    """d^2 f_i / dp_j dp_k, shape (P, P, N)."""
+    lib = _load()
+    pp = _f64(p)
+    P, N = nparams(model), W * H
+    d2 = np.empty((P, P, N))
+    lib.or_profile_second(model, W, H, _p(pp), _p(d2))
+    return d2
+
+
+def backward(model: int, W: int, H: int, g, p, alpha: float, beta: float, upstream):
+    """Implicit-function-theorem VJP of one fit: d loss / d g (N values), or None."""
+    lib = _load()
+    g, pp, up = _f64(g), _f64(p), _f64(upstream)
+    assert up.size == 7
+    out = np.empty(W * H)
+    if lib.or_backward(model, W, H, _p(g), _p(pp), float(alpha), float(beta), _p(up), _p(out)):
+        return None
     return out

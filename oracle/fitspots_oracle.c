@@ -425,3 +425,124 @@ int or_solve_damped(int P, const double *A16, const double *b, double lambda, do
         for (int k = 0; k < 4; ++k) A[j][k] = A16[4 * j + k];
     return solve_damped(P, A, b, lambda, delta);
 }
+
+/* ------------------------------------------------------------------------------------
+ * Backward pass by the implicit-function theorem (not in the paper; derived from Eq. 2).
+ * At a minimum of chi^2 over the full parameter vector q = (p, alpha, beta) the gradient
+ * -sum_i r_i K_i vanishes, with K_i = dh_i/dq = (alpha df_i/dp, f_i, 1) and r = g - h.
+ * Differentiating that condition in g_i gives dq/dg_i = M^-1 K_i with
+ *   M = sum_i K_i K_i^T - sum_i r_i d^2 h_i / dq^2,
+ * d^2 h/dp^2 = alpha d^2 f/dp^2, d^2 h/dp dalpha = df/dp, all other second derivatives 0.
+ * A vector-Jacobian product with upstream u is then grad_g_i = (M^-1 u) . K_i; the
+ * normalised chi^2 adds u_chi * 2 r_i / (N - P - 2) (its g-derivative at the minimum).
+ * ------------------------------------------------------------------------------------ */
+
+/* Second derivatives d2[(j*P+k)*N + i] = d^2 f_i / dp_j dp_k of the profile. */
+void or_profile_second(int model, int W, int H, const double *p, double *d2)
+{
+    const int N = W * H, P = or_nparams(model);
+    for (int i = 0; i < N; ++i) {
+        const double x = (double)(i % W), y = (double)(i / W);
+        const double dx = x - p[0], dy = y - p[1];
+        double h[4][4];
+        if (model == OR_MODEL_ISO) {
+            const double s = p[2], s2 = s * s, q = dx * dx + dy * dy;
+            const double f = exp(-q / (2.0 * s2));
+            h[0][0] = (dx * dx / (s2 * s2) - 1.0 / s2) * f;
+            h[1][1] = (dy * dy / (s2 * s2) - 1.0 / s2) * f;
+            h[0][1] = h[1][0] = dx * dy / (s2 * s2) * f;
+            h[0][2] = h[2][0] = (dx * q / (s2 * s2 * s) - 2.0 * dx / (s2 * s)) * f;
+            h[1][2] = h[2][1] = (dy * q / (s2 * s2 * s) - 2.0 * dy / (s2 * s)) * f;
+            h[2][2] = (q * q / (s2 * s2 * s2) - 3.0 * q / (s2 * s2)) * f;
+        } else {
+            const double sx = p[2], sy = p[3], sx2 = sx * sx, sy2 = sy * sy;
+            const double f = exp(-dx * dx / (2.0 * sx2) - dy * dy / (2.0 * sy2));
+            const double ax = dx / sx2, ay = dy / sy2;                 /* d ln f / d x0, y0 */
+            const double bx = dx * dx / (sx2 * sx), by = dy * dy / (sy2 * sy); /* d ln f / d sx, sy */
+            h[0][0] = (ax * ax - 1.0 / sx2) * f;
+            h[1][1] = (ay * ay - 1.0 / sy2) * f;
+            h[0][1] = h[1][0] = ax * ay * f;
+            h[0][2] = h[2][0] = (ax * bx - 2.0 * dx / (sx2 * sx)) * f;
+            h[1][3] = h[3][1] = (ay * by - 2.0 * dy / (sy2 * sy)) * f;
+            h[0][3] = h[3][0] = ax * by * f;
+            h[1][2] = h[2][1] = ay * bx * f;
+            h[2][2] = (bx * bx - 3.0 * dx * dx / (sx2 * sx2)) * f;
+            h[3][3] = (by * by - 3.0 * dy * dy / (sy2 * sy2)) * f;
+            h[2][3] = h[3][2] = bx * by * f;
+        }
+        for (int j = 0; j < P; ++j)
+            for (int k = 0; k < P; ++k) d2[((size_t)j * P + k) * N + i] = h[j][k];
+    }
+}
+
+/* Solve A x = b (n <= 6) by Gaussian elimination with partial pivoting; -1 if singular. */
+static int solve_dense(int n, double A[6][6], double *b)
+{
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (!(fabs(A[piv][c]) > 0.0) || !isfinite(A[piv][c])) return -1;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            const double m = A[r][c] / A[c][c];
+            for (int k = c; k < n; ++k) A[r][k] -= m * A[c][k];
+            b[r] -= m * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double t = b[r];
+        for (int k = r + 1; k < n; ++k) t -= A[r][k] * b[k];
+        b[r] = t / A[r][r];
+    }
+    return 0;
+}
+
+/* Vector-Jacobian product of one fit. p (4 values; isotropic uses p[2]), alpha, beta:
+ * the fitted point. upstream[7] = d loss / d (x0, y0, s_x, s_y, alpha, beta, chi2_norm);
+ * for the isotropic model the fitted sigma is reported in slots 2 and 3, so its upstream
+ * is upstream[2] + upstream[3]. grad_g receives N values. Returns 0, or -1 if M is
+ * singular. */
+int or_backward(int model, int W, int H, const double *g, const double *p, double alpha,
+                double beta, const double *upstream, double *grad_g)
+{
+    const int N = W * H, P = or_nparams(model), Q = P + 2;
+    double f[OR_MAX_PIXELS], d[4 * OR_MAX_PIXELS], d2[16 * OR_MAX_PIXELS];
+    or_profile(model, W, H, p, f, d);
+    or_profile_second(model, W, H, p, d2);
+    double M[6][6] = {{0}}, v[6];
+    for (int i = 0; i < N; ++i) {
+        double K[6];
+        for (int j = 0; j < P; ++j) K[j] = alpha * d[(size_t)j * N + i];
+        K[P] = f[i];
+        K[P + 1] = 1.0;
+        const double r = g[i] - (alpha * f[i] + beta);
+        for (int a = 0; a < Q; ++a)
+            for (int b = 0; b < Q; ++b) M[a][b] += K[a] * K[b];
+        for (int j = 0; j < P; ++j) {
+            for (int k = 0; k < P; ++k) M[j][k] -= r * alpha * d2[((size_t)j * P + k) * N + i];
+            M[j][P] -= r * d[(size_t)j * N + i];
+            M[P][j] -= r * d[(size_t)j * N + i];
+        }
+    }
+    if (model == OR_MODEL_ISO) {
+        v[0] = upstream[0];
+        v[1] = upstream[1];
+        v[2] = upstream[2] + upstream[3];
+    } else {
+        for (int j = 0; j < 4; ++j) v[j] = upstream[j];
+    }
+    v[P] = upstream[4];
+    v[P + 1] = upstream[5];
+    if (solve_dense(Q, M, v)) return -1;
+    const double cchi = 2.0 * upstream[6] / (double)(N - P - 2);
+    for (int i = 0; i < N; ++i) {
+        double t = v[P] * f[i] + v[P + 1];
+        for (int j = 0; j < P; ++j) t += v[j] * alpha * d[(size_t)j * N + i];
+        grad_g[i] = t + cchi * (g[i] - (alpha * f[i] + beta));
+    }
+    return 0;
+}

@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, Cla
   constexpr int TS2 = 2 * R + 2;
   constexpr int RS = red_stride(L);
   constexpr float yc0 = 0.5f * (float)R;  // origin of the row weights y~ = y - R/2
+  constexpr int kChunk = L < 8 ? L : 8;   // items a group claims per atomic
   static_assert(S * L == 32, "lane groups must tile a warp");
   extern __shared__ float4 smem4[];
   float *sw = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * warp_smem_floats(L, R);
@@ -274,6 +275,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, Cla
 
     float g[C][R];
     bool active = false, idle = cnt == 0;
+    int cbase = 0, cnext = 0, cend = 0;  // the group's claimed chunk of items
+    int cspot = 0, cwh = 0, cmod = 0;    // schedule entry held by thread j of the chunk
+    int64_t coff = 0;
     int spot = 0, W = 0, H = 0, P = 4;
     bool iso = false;
     float Nf = 0.f, Gs = 0.f, shift = 0.f;
@@ -294,25 +298,53 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, Cla
     while (true) {
       // -------------------------------------------------------------- refill the slot
       if (!active && !idle) {
-        int item = 0;
-        if (lg == 0) item = atomicAdd(a.cursors + cls, 1);
-        item = __shfl_sync(gmask, item, gi * L);
-        if (item >= cnt) {
+        if (cnext >= cend) {
+          // claim the next kChunk items of this class; thread j of the group keeps the
+          // schedule entry of item j (spot, offset, size, model)
+          int base = 0;
+          if (lg == 0) base = atomicAdd(a.cursors + cls, kChunk);
+          base = __shfl_sync(gmask, base, gi * L);
+          cbase = base;
+          cnext = base;
+          cend = min(base + kChunk, cnt);
+          if (lg < kChunk && base + lg < cnt) {
+            const int it_ = base + lg;
+            if (a.uniform) {
+              cspot = it_;
+              coff = (int64_t)it_ * (a.uw * a.uh);
+              cwh = (a.uw << 8) | a.uh;
+              cmod = a.umodel;
+            } else {
+              cspot = a.perm[beg + it_];
+              coff = a.offsets[cspot];
+              cwh = (a.dims[2 * cspot] << 8) | a.dims[2 * cspot + 1];
+              cmod = a.model[cspot];
+            }
+          }
+        }
+        if (cnext >= cnt) {
           idle = true;
         } else {
-          int64_t off;
-          if (a.uniform) {
-            spot = item;
-            W = a.uw;
-            H = a.uh;
-            iso = a.umodel == FS_MODEL_ISO;
-            off = (int64_t)spot * (W * H);
-          } else {
-            spot = a.perm[beg + item];
-            W = a.dims[2 * spot];
-            H = a.dims[2 * spot + 1];
-            iso = a.model[spot] == FS_MODEL_ISO;
-            off = a.offsets[spot];
+          const int src = gi * L + (cnext - cbase);
+          spot = __shfl_sync(gmask, cspot, src);
+          const int64_t off = __shfl_sync(gmask, coff, src);
+          const int wh = __shfl_sync(gmask, cwh, src);
+          W = wh >> 8;
+          H = wh & 255;
+          iso = __shfl_sync(gmask, cmod, src) == FS_MODEL_ISO;
+          ++cnext;
+          if (cnext < cend) {
+            // warm L2 with the next spot of the chunk (pixels and start values)
+            const int nsrc = gi * L + (cnext - cbase);
+            const int nspot = __shfl_sync(gmask, cspot, nsrc);
+            const int64_t noff = __shfl_sync(gmask, coff, nsrc);
+            const int nwh = __shfl_sync(gmask, cwh, nsrc);
+            const int esz = a.dtype == FS_U16 ? 2 : 4;
+            const char *nb = static_cast<const char *>(a.images) + noff * esz;
+            const int nbytes = (nwh >> 8) * (nwh & 255) * esz;
+            for (int line = lg; line * 128 < nbytes; line += L)  // addresses inside the spot
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + line * 128));
+            if (lg == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.init + 4 * nspot));
           }
           P = iso ? 3 : 4;
           if (a.dtype == FS_U16) {
@@ -504,9 +536,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, Cla
 
       // -------------------------------------------------------------- chi^2 change
       // delta = chi_t^2 - chi_b^2, refined near the two decision thresholds. The window
-      // covers the FP32 error of each chi^2: the rounding of alpha f in every residual
-      // adds at most 2 eps |alpha| sqrt(chi^2 F(bold)) (Cauchy-Schwarz), taken twice here.
-      const float noise = 4.f * 5.9604645e-8f * fabsf(alpha) * sqrtf(fmaxf(chi, 0.f) * FF);
+      // covers the FP32 error of each chi^2: rounding alpha f and the profile in every
+      // residual u gives errors of ~eps |alpha| f per pixel, i.e. a chi^2 error of about
+      // 6 eps |alpha| sqrt(chi^2 F(bold) / N); the window takes four times that per point.
+      const float noise =
+          24.f * 5.9604645e-8f * fabsf(alpha) * sqrtf(fmaxf(chi, 0.f) * FF * __fdividef(1.f, Nf));
       float delta = chi - chib;
       const float win = kTieWindow * chib + noise + noiseb;
       if (!first_eval && isfinite(chi) && isfinite(chib) && delta >= -a.min_delta * chib - win &&

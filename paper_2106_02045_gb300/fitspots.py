@@ -45,6 +45,9 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_uniform_workspace.restype = sz
         lib.fit_spots_config_fits.argtypes = [i, i]
         lib.fit_spots_config_fits.restype = i
+        lib.fit_spots_backward.argtypes = [vp, i, i64, vp, vp, vp, i64, vp, vp, vp, vp,
+                                           vp, vp, vp, vp, vp, vp]
+        lib.fit_spots_backward.restype = i
         lib.fit_spots_workspace.argtypes = [i64]
         lib.fit_spots_workspace.restype = sz
         lib.fit_spots_strerror.argtypes = [i]
@@ -203,3 +206,73 @@ def config_fits(size_class: int, config: int) -> bool:
 
 def set_config(size_class: int, config: int) -> None:
     check(library().fit_spots_set_config(int(size_class), int(config)), "fit_spots_set_config")
+
+
+def backward(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
+             model: torch.Tensor, fit_out: dict, grad_params=None, grad_alpha=None,
+             grad_beta=None, grad_chi2=None, grad_images: torch.Tensor | None = None,
+             stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """d loss / d images for upstream gradients of a fit (implicit-function theorem)."""
+    dev = images.device
+    dtype = U16 if images.dtype == torch.uint16 else F32
+    n = int(offsets.numel())
+    if grad_images is None:
+        grad_images = torch.zeros(images.numel(), dtype=torch.float32, device=dev)
+
+    def opt(t, shape):
+        if t is None:
+            return None
+        t = t.to(device=dev, dtype=torch.float32).contiguous()
+        if t.numel() != shape:
+            raise FitSpotsError("upstream gradient has the wrong size")
+        return t
+    gp, ga = opt(grad_params, 4 * n), opt(grad_alpha, n)
+    gb, gc = opt(grad_beta, n), opt(grad_chi2, n)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = library().fit_spots_backward(
+            _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(model), n,
+            _ptr(fit_out["params"]), _ptr(fit_out["alpha"]), _ptr(fit_out["beta"]),
+            _ptr(fit_out["state"]), _ptr(gp), _ptr(ga), _ptr(gb), _ptr(gc), _ptr(grad_images),
+            ctypes.c_void_p(s.cuda_stream))
+    check(rc, "fit_spots_backward")
+    return grad_images
+
+
+class FitSpotsFunction(torch.autograd.Function):
+    """Differentiable batched fit: (images, init) -> (params, alpha, beta, chi2).
+
+    The backward pass is the implicit-function-theorem kernel; the gradient with respect
+    to the start parameters is zero (the minimum does not depend on where the search
+    started). state and iters are returned as non-differentiable tensors."""
+
+    @staticmethod
+    def forward(ctx, images, init, offsets, dims, model, max_iter=20, max_error=0.0,
+                min_delta=1e-6, min_step=1e-4):
+        out = fit(images.detach(), offsets, dims, init.detach().contiguous(), model,
+                  max_iter=max_iter, max_error=max_error, min_delta=min_delta,
+                  min_step=min_step)
+        ctx.save_for_backward(images.detach(), offsets, dims, model, out["params"], out["alpha"],
+                              out["beta"], out["state"])
+        ctx.init_shape = init.shape
+        ctx.mark_non_differentiable(out["state"], out["iters"])
+        return out["params"], out["alpha"], out["beta"], out["chi2"], out["state"], out["iters"]
+
+    @staticmethod
+    def backward(ctx, g_params, g_alpha, g_beta, g_chi2, g_state, g_iters):
+        images, offsets, dims, model, params, alpha, beta, state = ctx.saved_tensors
+        grad_images = None
+        if ctx.needs_input_grad[0]:
+            fo = dict(params=params, alpha=alpha, beta=beta, state=state)
+            grad_images = backward(images, offsets, dims, model, fo, g_params, g_alpha, g_beta,
+                                   g_chi2).view(images.shape)
+        grad_init = torch.zeros(ctx.init_shape, dtype=torch.float32, device=params.device) \
+            if ctx.needs_input_grad[1] else None
+        return grad_images, grad_init, None, None, None, None, None, None, None
+
+
+def fit_differentiable(images, init, offsets, dims, model, **kw):
+    """FitSpotsFunction.apply with keyword tolerances."""
+    return FitSpotsFunction.apply(images, init, offsets, dims, model, kw.get("max_iter", 20),
+                                  kw.get("max_error", 0.0), kw.get("min_delta", 1e-6),
+                                  kw.get("min_step", 1e-4))

@@ -1,0 +1,128 @@
+"""GPU implicit-function-theorem backward vs the FP64 oracle's backward (each at its own
+fit of the same pixels), the invariance identities, and the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2106_02045_gb300 import fitspots, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+TIGHT = dict(max_iter=50, min_delta=0.0, min_step=1e-6)   # tight stop FP32 can reach
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _upstream(n, seed):
+    g = torch.Generator().manual_seed(seed)
+    return (torch.randn(n, 4, generator=g), torch.randn(n, generator=g),
+            torch.randn(n, generator=g), torch.randn(n, generator=g))
+
+
+def test_backward_matches_oracle_ift_on_iso16():
+    """16x16 isotropic spots (the backward workload): per-spot relative error of the
+    pixel gradient against the oracle's FP64 backward <= 1e-4 on determined spots."""
+    import oracle
+    n = 1024
+    b = synth.make_workload("iso16", n)
+    g = b.to(DEV)
+    out = fitspots.fit_batch(g, **TIGHT)
+    gp, ga, gb, gc = _upstream(n, 3)
+    grad = fitspots.backward(g.images, g.offsets, g.dims, g.model, out, gp, ga, gb, gc)
+    torch.cuda.synchronize()
+    grad = grad.cpu().numpy()
+    d = b.numpy()
+    img = synth.as_numpy_images(b)
+    ref = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"], max_iter=300,
+                           min_delta=0.0, min_step=1e-13)
+    errs = []
+    for s in range(n):
+        off = int(d["offsets"][s])
+        gs = img[off:off + 256].astype(np.float64)
+        up = np.concatenate([gp[s].numpy(), [ga[s], gb[s], gc[s]]]).astype(np.float64)
+        ro = oracle.backward(0, 16, 16, gs, ref["params"][s], ref["alpha"][s], ref["beta"][s], up)
+        assert ro is not None
+        errs.append(np.linalg.norm(grad[off:off + 256] - ro) / np.linalg.norm(ro))
+    errs = np.array(errs)
+    st = out["state"].cpu().numpy()
+    print(f"iso16 backward: median rel err {np.median(errs):.2e}, p99 {np.percentile(errs, 99):.2e}, "
+          f"max {errs.max():.2e}; GPU states {np.unique(st, return_counts=True)}; "
+          f"states of the worst: {st[np.argsort(errs)[-5:]]}")
+    assert np.isin(st, fitspots.CONVERGED_STATES).mean() >= 0.999
+    assert np.mean(errs <= 1e-4) >= 0.999
+    assert np.median(errs) <= 1e-5
+
+
+def test_backward_identities_both_models():
+    """Shift and scale invariance of the fit fix sum_i dq/dg_i and sum_i g_i dq/dg_i."""
+    for name in ("iso16", "ell32"):
+        b = synth.make_workload(name, 256, device=DEV)   # ell32 stays uint16
+        out = fitspots.fit_batch(b, **TIGHT)
+        conv = torch.isin(out["state"], torch.tensor(fitspots.CONVERGED_STATES, device=DEV,
+                                                     dtype=torch.int32))
+        N = int(b.dims[0, 0] * b.dims[0, 1])
+        gimg = b.images.to(torch.float32).view(b.n, N).double()
+        for k, name_k in enumerate(("x0", "y0", "sx", "sy", "alpha", "beta", "chi2")):
+            if name == "iso16" and k == 3:
+                continue
+            gp = torch.zeros(b.n, 4, device=DEV)
+            ga = torch.zeros(b.n, device=DEV)
+            gb = torch.zeros(b.n, device=DEV)
+            gc = torch.zeros(b.n, device=DEV)
+            if k < 4:
+                gp[:, k] = 1.0
+            elif k == 4:
+                ga[:] = 1.0
+            elif k == 5:
+                gb[:] = 1.0
+            else:
+                gc[:] = 1.0
+            grad = fitspots.backward(b.images, b.offsets, b.dims, b.model, out, gp, ga, gb, gc)
+            G = grad.view(b.n, N).double()
+            s1 = G.sum(1)[conv]
+            sg = (G * gimg).sum(1)[conv]
+            scale = G.abs().sum(1)[conv] + 1e-30
+            sgscale = (G * gimg).abs().sum(1)[conv] + 1e-30
+            if k < 4:
+                exp1, expg = torch.zeros_like(s1), torch.zeros_like(sg)
+            elif k == 4:
+                exp1, expg = torch.zeros_like(s1), out["alpha"].double()[conv]
+            elif k == 5:
+                exp1, expg = torch.ones_like(s1), out["beta"].double()[conv]
+            else:
+                exp1, expg = torch.zeros_like(s1), 2 * out["chi2"].double()[conv]
+            e1 = ((s1 - exp1).abs() / scale).max().item()
+            eg = ((sg - expg).abs() / sgscale).max().item()
+            print(f"{name} {name_k}: identity errors {e1:.1e} {eg:.1e}")
+            assert e1 < 2e-4 and eg < 2e-4, (name, name_k, e1, eg)
+
+
+def test_autograd_function_and_zero_paths():
+    b = synth.make_workload("iso15", 200, device=DEV)
+    images = b.images.clone().requires_grad_(True)
+    init = b.init.clone().requires_grad_(True)
+    params, alpha, beta, chi2, state, iters = fitspots.fit_differentiable(
+        images, init, b.offsets, b.dims, b.model)
+    w = torch.randn(params.shape, device=DEV)
+    loss = (params * w).sum() + 0.5 * alpha.sum() - beta.sum() + chi2.sum()
+    gi, gin = torch.autograd.grad(loss, (images, init))
+    direct = fitspots.backward(b.images, b.offsets, b.dims, b.model,
+                               dict(params=params.detach(), alpha=alpha.detach(),
+                                    beta=beta.detach(), state=state),
+                               w, torch.full_like(alpha, 0.5), torch.full_like(beta, -1.0),
+                               torch.ones_like(chi2))
+    assert torch.equal(gi, direct.view(gi.shape))
+    assert torch.count_nonzero(gin) == 0
+    # a spot stopped by the iteration budget is not at a minimum: zero gradient
+    out = fitspots.fit_batch(b, max_iter=1)
+    grad = fitspots.backward(b.images, b.offsets, b.dims, b.model, out,
+                             torch.ones(b.n, 4, device=DEV))
+    G = grad.view(b.n, -1)
+    not_conv = out["state"] == 0
+    assert not_conv.any()
+    assert torch.count_nonzero(G[not_conv]) == 0

@@ -1,0 +1,106 @@
+"""Pins of the oracle's implicit-function-theorem backward pass (no GPU needed): second
+derivatives against finite differences, the vector-Jacobian product against finite
+differences of polished FP64 fits, and the exact identities that translation and scale
+invariance of the fit impose."""
+import numpy as np
+import pytest
+
+ISO, ELL = 0, 1
+
+
+def _spot(model, W, H, p, amp, bg, rng):
+    x, y = np.arange(W)[None, :], np.arange(H)[:, None]
+    sy = p[2] if model == ISO else p[3]
+    f = np.exp(-0.5 * ((x - p[0]) / p[2]) ** 2 - 0.5 * ((y - p[1]) / sy) ** 2).ravel()
+    return rng.poisson(amp * f + bg).astype(np.float64)
+
+
+def _polished_fit(oracle_mod, model, W, H, g, p0):
+    o = oracle_mod.fit_spots(g, np.array([0]), np.array([[W, H]], np.int32),
+                             np.array([p0], np.float32), np.array([model], np.uint8),
+                             max_iter=300, min_delta=0.0, min_step=1e-13)
+    return o["params"][0], o["alpha"][0], o["beta"][0], o["chi2"][0], o["state"][0]
+
+
+@pytest.mark.parametrize("model", [ISO, ELL])
+def test_second_derivatives_match_finite_differences(oracle_mod, model):
+    rng = np.random.default_rng(20)
+    for _ in range(6):
+        W, H = int(rng.integers(5, 20)), int(rng.integers(5, 20))
+        p = np.array([rng.uniform(1, W - 2), rng.uniform(1, H - 2), rng.uniform(0.9, 3),
+                      rng.uniform(0.9, 3)])
+        if model == ISO:
+            p[3] = p[2]
+        d2 = oracle_mod.profile_second(model, W, H, p)
+        P = d2.shape[0]
+        for k in range(P):
+            h = 1e-6 * max(1.0, abs(p[k]))
+            pp, pm = p.copy(), p.copy()
+            pp[k] += h
+            pm[k] -= h
+            if model == ISO and k == 2:
+                pp[3], pm[3] = pp[2], pm[2]
+            _, dp = oracle_mod.profile(model, W, H, pp, with_derivs=True)
+            _, dm = oracle_mod.profile(model, W, H, pm, with_derivs=True)
+            fd = (dp - dm) / (2 * h)                 # d/dp_k of df/dp_j, shape (P, N)
+            for j in range(P):
+                assert np.max(np.abs(fd[j] - d2[j, k])) <= 1e-6 * (np.max(np.abs(d2[j, k])) + 1e-3)
+
+
+@pytest.mark.parametrize("model,W,H", [(ISO, 9, 9), (ELL, 11, 8), (ISO, 16, 16)])
+def test_backward_matches_finite_differences(oracle_mod, model, W, H):
+    """VJP of the fitted (x0, y0, s, [sy], alpha, beta, chi2_n) against central finite
+    differences of polished refits, per pixel, to 1e-4 relative."""
+    rng = np.random.default_rng(21 + W)
+    for trial in range(3):
+        p = np.array([(W - 1) / 2 + rng.uniform(-0.7, 0.7), (H - 1) / 2 + rng.uniform(-0.7, 0.7),
+                      rng.uniform(1.2, 1.8), rng.uniform(1.2, 1.8)])
+        if model == ISO:
+            p[3] = p[2]
+        g = _spot(model, W, H, p, 1500.0, 80.0, rng)
+        q, a, b, c, st = _polished_fit(oracle_mod, model, W, H, g, p)
+        assert st in (1, 2, 4)
+        up = rng.normal(size=7)
+        if model == ISO:
+            up[3] = 0.0
+        grad = oracle_mod.backward(model, W, H, g, q, a, b, up)
+        N = W * H
+        fd = np.empty(N)
+        for i in range(N):
+            h = 1e-2 * max(1.0, abs(g[i]) ** 0.5)
+            vals = []
+            for sgn in (1.0, -1.0):
+                gg = g.copy()
+                gg[i] += sgn * h
+                qq, aa, bb, cc, _ = _polished_fit(oracle_mod, model, W, H, gg, q)
+                vals.append(up[:4] @ qq + up[4] * aa + up[5] * bb + up[6] * cc)
+            fd[i] = (vals[0] - vals[1]) / (2 * h)
+        assert np.linalg.norm(grad - fd) <= 1e-4 * np.linalg.norm(fd), (trial, np.linalg.norm(grad - fd) / np.linalg.norm(fd))
+
+
+@pytest.mark.parametrize("model", [ISO, ELL])
+def test_backward_invariance_identities(oracle_mod, model):
+    """Adding c to every pixel moves only beta by c; scaling pixels by s scales alpha, beta
+    by s, chi^2 by s^2 and leaves the shape alone. Hence sum_i dq/dg_i and
+    sum_i g_i dq/dg_i are fixed exactly."""
+    rng = np.random.default_rng(22)
+    W, H = 13, 12
+    p = np.array([6.3, 5.4, 1.6, 1.9])
+    if model == ISO:
+        p[3] = p[2]
+    g = _spot(model, W, H, p, 900.0, 60.0, rng)
+    q, a, b, c, st = _polished_fit(oracle_mod, model, W, H, g, p)
+    slots = [0, 1, 2] if model == ISO else [0, 1, 2, 3]
+    for k in slots + [4, 5, 6]:
+        up = np.zeros(7)
+        up[k] = 1.0
+        grad = oracle_mod.backward(model, W, H, g, q, a, b, up)
+        s1, sg = grad.sum(), (g * grad).sum()
+        if k in slots:            # shape parameters: invariant under both
+            assert abs(s1) < 1e-9 and abs(sg) < 1e-7
+        elif k == 4:              # alpha: shift-invariant, scales with s
+            assert abs(s1) < 1e-9 and abs(sg - a) < 1e-7 * abs(a)
+        elif k == 5:              # beta: moves with the shift, scales with s
+            assert abs(s1 - 1.0) < 1e-9 and abs(sg - b) < 1e-7 * abs(b)
+        else:                     # normalised chi^2: shift-invariant, scales with s^2
+            assert abs(s1) < 1e-7 and abs(sg - 2 * c) < 1e-7 * c

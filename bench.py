@@ -284,15 +284,99 @@ def run(args) -> None:
     if not args.no_cpu_baseline:
         bcpu = b.head(args.cpu_sample).to("cpu")
         cpu = _cpu_baseline(bcpu, args.cpu_sample)
+    extras = {} if args.no_extras else _extras(args, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_job / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": _config(world, n_spots), "clocks": clocks,
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "fits_per_step": n_spots * world, "converged_fraction": conv / n_spots}
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed(fn, steps, stream):
+    """Mean CUDA-event time (ms) of fn() over `steps` runs on `stream`, after 3 warm-ups."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _extras(args, dev) -> dict:
+    """The other hot-path rows on their workloads: mixed sizes, backward, serving."""
+    import numpy as np
+    import torch
+    from paper_2106_02045_gb300 import fitspots, serving, synth
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    hbm = 6691.8
+    try:
+        hbm = float(json.loads((ROOT / "MEASURED_PEAKS.json").read_text())["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    # mixed sizes 5..32, both models, 2,000,000 spots (fit_spots with the size-class prepass)
+    mb = synth.make_workload("mixed", args.mixed_spots, device=dev)
+    mo = fitspots.alloc_outputs(mb.n, dev)
+    mws = torch.empty(fitspots.workspace_bytes(mb.n), dtype=torch.uint8, device=dev)
+    ms = _timed(lambda: fitspots.fit_batch(mb, out=mo, workspace=mws, stream=stream), 3, stream)
+    conv = int(torch.isin(mo["state"], torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())
+    out["mixed"] = {"workload": f"mixed: {mb.n:,} spots, W,H ~ U{{5..32}}, models 50/50, FP32",
+                    "value": conv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                    "launches_per_step": "memset + 3 prepass + one persistent launch per "
+                                         "configuration in use"}
+    del mb, mo, mws
+    # backward: 262,144 spots of 16x16, implicit-function-theorem VJP
+    bb = synth.make_workload("iso16", None, device=dev)
+    fo = fitspots.fit_batch(bb, max_iter=50, min_delta=0.0, min_step=1e-6)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    up = [torch.randn(bb.n, 4, generator=gen, device=dev)] + \
+         [torch.randn(bb.n, generator=gen, device=dev) for _ in range(3)]
+    gimg = torch.zeros(bb.images.numel(), dtype=torch.float32, device=dev)
+    bms = _timed(lambda: fitspots.backward(bb.images, bb.offsets, bb.dims, bb.model, fo, *up,
+                                           grad_images=gimg, stream=stream), 10, stream)
+    nbytes = bb.n * (256 * 8 + 73)
+    out["backward"] = {"workload": f"iso16: {bb.n:,} spots, 16x16 FP32, isotropic, VJP of all "
+                                   "outputs w.r.t. all pixels",
+                       "value": bb.n / (bms * 1e-3), "unit": "spots/s", "ms_per_step": bms,
+                       "roofline": {"bound": "hbm", "achieved": nbytes / (bms * 1e-3) / 1e9,
+                                    "peak": hbm, "unit": "GB/s",
+                                    "frac": nbytes / (bms * 1e-3) / 1e9 / hbm,
+                                    "bytes_per_spot": 256 * 8 + 73,
+                                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    del bb, fo, gimg
+    # serving: 2048x2048 uint16 frames at 2000 fps, 64 markers, 21x21 ROIs cut on device
+    cs = synth.make_camera_stream(args.serving_ring, 64, 2048, 2048, device=dev)
+    host = torch.empty(cs.frames.shape, dtype=torch.uint16, pin_memory=True)
+    host.copy_(cs.frames)
+    srv = serving.TrackingServer(2048, 2048, markers=64, sessions=1, device=dev)
+    srv.set_markers(0, cs.start)
+    warm = args.serving_warmup
+    nfr = warm + args.serving_frames
+    t0 = time.perf_counter()
+    serving.run_stream(srv, 0, host, nfr, fps=2000.0)
+    wall = time.perf_counter() - t0
+    lat = np.array([srv.logs[0].latency[k] for k in range(warm, nfr) if k in srv.logs[0].latency])
+    summ = serving.latency_summary(lat)
+    truth = cs.truth.cpu().numpy()
+    err = np.concatenate([np.hypot(*(srv.logs[0].results[k][:, :2] - truth[k % args.serving_ring]).T)
+                          for k in range(warm, nfr) if k in srv.logs[0].results])
+    out["serving"] = {"workload": "2048x2048 uint16 camera at 2000 fps, 64 fiducials, 21x21 ROIs "
+                                  "cut on device, warm-started isotropic fits, drift 0.05 px/frame",
+                      "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "max_ms": summ["max_ms"],
+                      "frames": summ["frames"], "warmup_frames": warm, "dropped": srv.dropped,
+                      "sustained_fps": nfr / wall, "tracking_error_px_median": float(np.median(err)),
+                      "latency": "host arrival stamp -> results on host; one CUDA graph per frame"}
+    return out
 
 
 def _e2e(args, b, out, ws, stream, barrier, world, dev):
@@ -353,6 +437,11 @@ def main() -> None:
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
+    ap.add_argument("--mixed-spots", type=int, default=2_000_000)
+    ap.add_argument("--serving-frames", type=int, default=20000)
+    ap.add_argument("--serving-warmup", type=int, default=1000)
+    ap.add_argument("--serving-ring", type=int, default=128)
     ap.add_argument("--spots", type=int, default=N_SPOTS, help="spots per GPU (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -175,6 +175,36 @@ int fit_spots_backward(const void *images, int dtype, int64_t image_elems,
                        const float *grad_beta, const float *grad_chi2, float *grad_images,
                        void *stream);
 
+/*
+ * Serving (real-time fiducial tracking; the paper's motivation of stabilising a sample
+ * at millisecond time scales by following sparse fiducial spots, Sec. "Introduction").
+ * A batch covers up to max_batch frames of different sessions; desc (device int32
+ * [1 + 2 * max_batch]) = count, then (frame slot, session) per batch entry.
+ *
+ * fs_serve_roi_cut: for every entry b < count and marker m, cut the roi x roi block of
+ * frame slot desc[1+2b] (frames: device uint16 slots of frame_w x frame_h, slot s at
+ * frames + s*frame_w*frame_h) at the rounded previous centre state[session][m] (device
+ * float [sessions][markers][4] = x, y, sigma_x, sigma_y, frame coordinates), clamped into
+ * the frame, into rois[(b*markers + m) * roi*roi] (uint16), the warm start
+ * init[b*markers + m] (ROI coordinates) and origin[b*markers + m] = (x, y) of the block.
+ * roi must be 3..32 and fit in the frame. Entries b >= count are skipped.
+ *
+ * fs_serve_update: after fit_spots_uniform on the count*markers ROIs, move every marker
+ * whose fit converged (state MIN_DELTA, MIN_STEP, MAX_ERROR or NO_DECREASE, finite
+ * parameters) to origin + fitted centre (a lost marker keeps its last state), and write
+ * results[b*markers + m][8] = (x, y, sigma_x, sigma_y in frame coordinates, alpha, beta,
+ * normalised chi^2, fit state).
+ * Both enqueue one kernel on stream and allocate nothing; the graph of a serving step is
+ * cut -> fit -> update. Not in the paper (it names the use, not a serving design).
+ */
+int fs_serve_roi_cut(const uint16_t *frames, int frame_w, int frame_h, int roi, int markers,
+                     const int32_t *desc, int max_batch, const float *state, uint16_t *rois,
+                     float *init, int32_t *origin, void *stream);
+int fs_serve_update(const int32_t *desc, int max_batch, int markers, const float *params,
+                    const float *alpha, const float *beta, const float *chi2,
+                    const int32_t *fit_state, const int32_t *origin, float *state,
+                    float *results, void *stream);
+
 /* Message for an FS_ERR_* / FS_OK code (static storage). */
 const char *fit_spots_strerror(int code);
 

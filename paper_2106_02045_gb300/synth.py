@@ -273,6 +273,56 @@ def make_paper(n: int, S: int, signal: float, background: float, seed: int, devi
     return _pack_uniform(g, S, S, MODEL_ISO, init, truth, name)
 
 
+@dataclass
+class CameraStream:
+    """Synthetic camera frames with drifting fiducial markers (serving workload)."""
+
+    frames: torch.Tensor      # uint16 [n_frames, H, W]
+    truth: torch.Tensor       # float64 [n_frames, markers, 2] marker centres (x, y)
+    sigma: torch.Tensor       # float64 [markers]
+    start: torch.Tensor       # float32 [markers, 4] start state (x, y, s, s), ~0.3 px off
+
+
+def make_camera_stream(n_frames: int, markers: int = 64, width: int = 2048, height: int = 2048,
+                       seed: int = SEED_BASE + 5, device="cpu", photons: float = 20000.0,
+                       background: float = 100.0, drift: float = 0.05) -> CameraStream:
+    """uint16 frames: background + markers of sigma ~ U(1.2, 2.0) carrying ``photons``
+    each, Poisson + N(0, 2^2) read noise + offset 100; marker centres at least 16 px from
+    the border, moving as a Gaussian random walk of ``drift`` px per frame and axis."""
+    gen = _gen(seed, device)
+    f64 = torch.float64
+    x0 = 16 + (width - 33) * torch.rand(markers, generator=gen, device=device, dtype=f64)
+    y0 = 16 + (height - 33) * torch.rand(markers, generator=gen, device=device, dtype=f64)
+    sig = 1.2 + 0.8 * torch.rand(markers, generator=gen, device=device, dtype=f64)
+    steps = drift * torch.randn(n_frames, markers, 2, generator=gen, device=device, dtype=f64)
+    steps[0] = 0.0
+    pos = torch.stack([x0, y0], dim=1)[None] + torch.cumsum(steps, dim=0)
+    pos[..., 0].clamp_(14, width - 15)
+    pos[..., 1].clamp_(14, height - 15)
+    amp = photons / (2 * math.pi * sig * sig)
+    frames = torch.empty((n_frames, height, width), dtype=torch.uint16, device=device)
+    half = 12
+    ar = torch.arange(-half, half + 1, device=device)
+    for k in range(n_frames):
+        lam = torch.full((height, width), background, dtype=f64, device=device)
+        cx = torch.round(pos[k, :, 0]).long()
+        cy = torch.round(pos[k, :, 1]).long()
+        xs = (cx[:, None] + ar[None, :]).clamp(0, width - 1)              # [m, 25]
+        ys = (cy[:, None] + ar[None, :]).clamp(0, height - 1)
+        fx = torch.exp(-0.5 * ((xs - pos[k, :, 0:1]) / sig[:, None]) ** 2)
+        fy = torch.exp(-0.5 * ((ys - pos[k, :, 1:2]) / sig[:, None]) ** 2)
+        spot = amp[:, None, None] * fy[:, :, None] * fx[:, None, :]        # [m, 25, 25]
+        idx = (ys[:, :, None] * width + xs[:, None, :]).reshape(-1)
+        lam.view(-1).index_add_(0, idx, spot.reshape(-1))
+        noisy = torch.poisson(lam, generator=gen) + 2.0 * torch.randn(
+            lam.shape, generator=gen, device=device, dtype=f64) + 100.0
+        frames[k] = torch.round(noisy).clamp(0, 65535).to(torch.int32).to(torch.uint16)
+    off = 0.3 * (2 * torch.rand(markers, 2, generator=gen, device=device, dtype=f64) - 1)
+    start = torch.stack([pos[0, :, 0] + off[:, 0], pos[0, :, 1] + off[:, 1], sig * 1.1, sig * 1.1],
+                        dim=1).to(torch.float32)
+    return CameraStream(frames, pos, sig, start)
+
+
 def make_workload(name: str, n: int | None = None, device="cpu") -> SpotBatch:
     """One of ``WORKLOADS`` at its full size, or its first ``n`` draws at size n."""
     n = FULL_SIZES[name] if n is None else int(n)

@@ -243,15 +243,7 @@ def run(args) -> None:
     evals = int(out["evals"].sum())
     launches = args.steps  # one fit kernel per step (plus one workspace memset)
 
-    t = torch.tensor([ms_total, float(conv), float(n_spots)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms_job, conv_job = float(tmax[0]), float(tsum[1])
-    else:
-        ms_job, conv_job = ms_total, float(conv)
+    ms_job, conv_job = job_totals(ms_total, conv, world, dev)
     value = conv_job * args.steps / (ms_job * 1e-3)
 
     # ---------------------------------------------------------------- end to end
@@ -295,6 +287,20 @@ def run(args) -> None:
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def job_totals(ms: float, converged: float, world: int, device) -> tuple[float, float]:
+    """Whole-job time and work: the slowest rank's time (MAX) and all ranks' converged
+    fits (SUM). No collective touches the fit data; the ranks' spots are independent."""
+    if world <= 1:
+        return float(ms), float(converged)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(converged)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
 
 
 def _timed(fn, steps, stream):
@@ -414,15 +420,8 @@ def _e2e(args, b, out, ws, stream, barrier, world, dev):
     conv_e2e = int(np.isin(h_out["state"].numpy(), CONVERGED).sum())
     h2d = h_img.numel() * h_img.element_size() + h_init.numel() * h_init.element_size()
     d2h = sum(v.numel() * v.element_size() for v in h_out.values())
-    te = torch.tensor([e2e_ms, float(conv_e2e)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tm = te.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ts = te.clone()
-        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
-        e2e_value = float(ts[1]) / (float(tm[0]) * 1e-3)
-    else:
-        e2e_value = conv_e2e / (e2e_ms * 1e-3)
+    ms_max, conv_sum = job_totals(e2e_ms, conv_e2e, world, dev)
+    e2e_value = conv_sum / (ms_max * 1e-3)
 
     return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 

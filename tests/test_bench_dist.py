@@ -1,0 +1,44 @@
+"""The multi-rank bookkeeping of bench.py on CPU: two gloo ranks with different times and
+work; the job value is all ranks' fits over the slowest rank's time (weak scaling)."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms, conv = bench.job_totals(10.0 + 5.0 * rank, 1000.0 * (rank + 1), world, "cpu")
+    q.put((rank, ms, conv))
+    dist.destroy_process_group()
+
+
+def test_job_totals_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, ms, conv in got:
+        assert ms == 15.0 and conv == 3000.0
+
+
+def test_job_totals_single_rank_is_identity():
+    import bench
+    assert bench.job_totals(12.5, 42, 1, "cpu") == (12.5, 42.0)

@@ -340,6 +340,40 @@ def _extras(args, dev) -> dict:
                     "value": conv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                     "launches_per_step": "memset + 3 prepass + one persistent launch per "
                                          "configuration in use"}
+    # the plain alternative: one fit_spots_uniform launch per (W, H, model), the spots of
+    # each size stored back to back (the layout of the paper's kernel; the regrouping
+    # copies are not timed), launched one after another on the stream
+    key = (mb.dims[:, 0].to(torch.int64) * 64 + mb.dims[:, 1]) * 2 + mb.model.to(torch.int64)
+    groups = []
+    uws = torch.empty(max(fitspots.uniform_workspace_bytes(), 16), dtype=torch.uint8, device=dev)
+    for k in torch.unique(key).tolist():
+        idx = torch.nonzero(key == k).flatten()
+        gw, gh, gm = int(k // 2 // 64), int(k // 2 % 64), int(k % 2)
+        cols = mb.offsets[idx][:, None] + torch.arange(gw * gh, device=dev)[None, :]
+        groups.append((mb.images[cols.reshape(-1)].contiguous(), gw, gh, gm,
+                       mb.init[idx].contiguous(), fitspots.alloc_outputs(idx.numel(), dev)))
+
+    def per_size():
+        for imgs, gw, gh, gm, ini, o in groups:
+            fitspots.fit_uniform(imgs, gw, gh, gm, ini, out=o, workspace=uws, stream=stream)
+    pms = _timed(per_size, 3, stream)
+    out["mixed"]["one_launch_per_size"] = {
+        "ms_per_step": pms, "launches_per_step": len(groups),
+        "persistent_speedup": pms / ms,
+        "what": "one fit_spots_uniform launch per distinct (W, H, model), sizes back to back"}
+    del groups
+    # autotuned: every usable configuration timed per size class on a 4,096-spot sample
+    from paper_2106_02045_gb300 import autotune
+    t0 = time.perf_counter()
+    tuned = autotune.autotune(n=4096, reps=2, dtype=fitspots.F32, device=dev)
+    tune_s = time.perf_counter() - t0
+    ams = _timed(lambda: fitspots.fit_batch(mb, out=mo, workspace=mws, stream=stream), 3, stream)
+    aconv = int(torch.isin(mo["state"], torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())
+    out["mixed"]["autotuned"] = {"value": aconv / (ams * 1e-3), "ms_per_step": ams,
+                                 "tuning_s": tune_s,
+                                 "configs": {c: fitspots.configs()[r["config"]]
+                                             for c, r in tuned.items()}}
+    autotune.defaults()
     del mb, mo, mws
     # backward: 262,144 spots of 16x16, implicit-function-theorem VJP
     bb = synth.make_workload("iso16", None, device=dev)

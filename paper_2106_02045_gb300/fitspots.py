@@ -95,6 +95,10 @@ def workspace_bytes(n: int) -> int:
     return int(library().fit_spots_workspace(int(n)))
 
 
+def uniform_workspace_bytes() -> int:
+    return int(library().fit_spots_uniform_workspace())
+
+
 def alloc_outputs(n: int, device) -> dict:
     return dict(params=torch.empty((n, 4), dtype=torch.float32, device=device),
                 alpha=torch.empty(n, dtype=torch.float32, device=device),

@@ -43,6 +43,8 @@ SMS, LANES_PER_SM = 152, 128
 CONVERGED = (1, 2, 3, 4)
 PROFILE = ROOT / "profiles" / "fit_kernel_ell32.md"
 SOURCE = ROOT / "paper_2106_02045_gb300" / "csrc" / "fitspots.cu"
+BWD_SOURCE = ROOT / "paper_2106_02045_gb300" / "csrc" / "backward.cu"
+BWD_PROFILE = ROOT / "profiles" / "backward_iso16.md"
 
 
 def _dist_env():
@@ -119,13 +121,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile() -> float | None:
+def _traffic_from_profile(profile=None, source=None) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
-    if not PROFILE.exists():
+    profile = PROFILE if profile is None else profile
+    source = SOURCE if source is None else source
+    if not profile.exists():
         return None
-    sha = hashlib.sha256(SOURCE.read_bytes()).hexdigest()[:16]
+    sha = hashlib.sha256(source.read_bytes()).hexdigest()[:16]
     per_launch, src = None, None
-    for line in PROFILE.read_text().splitlines():
+    for line in profile.read_text().splitlines():
         if line.startswith("traffic_bytes_per_full_launch:"):
             per_launch = float(line.split(":", 1)[1].split()[0])
         if line.startswith("source_sha256_16:"):
@@ -241,6 +245,7 @@ def run(args) -> None:
     state = out["state"]
     conv = int(torch.isin(state, torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())
     evals = int(out["evals"].sum())
+    iters = int(out["iters"].sum())
     launches = args.steps  # one fit kernel per step (plus one workspace memset)
 
     ms_job, conv_job = job_totals(ms_total, conv, world, dev)
@@ -270,13 +275,18 @@ def run(args) -> None:
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "T lane-op/s", "frac": achieved / peak, "traffic": traffic,
                 "ops_per_launch": ops, "evals_per_spot": evals / n_spots,
+                # the same time against the work of a direct per-pixel evaluation: 12 ops per
+                # pixel per evaluated point and 26 more per pixel at each gradient point
+                # (one per LM iteration), elliptic model
+                "direct_count": {"iters_per_spot": iters / n_spots,
+                                 "frac": float(evals * 12 + iters * 26) * W * H / kernel_s / peak},
                 "peak_source": f"derived: {SMS} SMs x {LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz",
                 "kernel": "fit_kernel (uniform 32x32)"}
     cpu = None
     if not args.no_cpu_baseline:
         bcpu = b.head(args.cpu_sample).to("cpu")
         cpu = _cpu_baseline(bcpu, args.cpu_sample)
-    extras = {} if args.no_extras else _extras(args, dev)
+    extras = {} if args.no_extras else _extras(args, dev, set(args.extras.split(",")))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_job / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -318,11 +328,9 @@ def _timed(fn, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def _extras(args, dev) -> dict:
+def _extras(args, dev, which=("mixed", "backward", "serving")) -> dict:
     """The other hot-path rows on their workloads: mixed sizes, backward, serving."""
-    import numpy as np
     import torch
-    from paper_2106_02045_gb300 import fitspots, serving, synth
     stream = torch.cuda.current_stream(dev)
     out = {}
     hbm = 6691.8
@@ -330,6 +338,19 @@ def _extras(args, dev) -> dict:
         hbm = float(json.loads((ROOT / "MEASURED_PEAKS.json").read_text())["hbm_gbs"])
     except (OSError, ValueError, KeyError):
         pass
+    if "mixed" in which:
+        out.update(_extra_mixed(args, dev, stream))
+    if "backward" in which:
+        out.update(_extra_backward(dev, stream, hbm))
+    if "serving" in which:
+        out.update(_extra_serving(args, dev))
+    return out
+
+
+def _extra_mixed(args, dev, stream) -> dict:
+    import torch
+    from paper_2106_02045_gb300 import fitspots, synth
+    out = {}
     # mixed sizes 5..32, both models, 2,000,000 spots (fit_spots with the size-class prepass)
     mb = synth.make_workload("mixed", args.mixed_spots, device=dev)
     mo = fitspots.alloc_outputs(mb.n, dev)
@@ -375,6 +396,12 @@ def _extras(args, dev) -> dict:
                                              for c, r in tuned.items()}}
     autotune.defaults()
     del mb, mo, mws
+    return out
+
+
+def _extra_backward(dev, stream, hbm) -> dict:
+    import torch
+    from paper_2106_02045_gb300 import fitspots, synth
     # backward: 262,144 spots of 16x16, implicit-function-theorem VJP
     bb = synth.make_workload("iso16", None, device=dev)
     fo = fitspots.fit_batch(bb, max_iter=50, min_delta=0.0, min_step=1e-6)
@@ -385,15 +412,23 @@ def _extras(args, dev) -> dict:
     bms = _timed(lambda: fitspots.backward(bb.images, bb.offsets, bb.dims, bb.model, fo, *up,
                                            grad_images=gimg, stream=stream), 10, stream)
     nbytes = bb.n * (256 * 8 + 73)
-    out["backward"] = {"workload": f"iso16: {bb.n:,} spots, 16x16 FP32, isotropic, VJP of all "
+    out_b = {"workload": f"iso16: {bb.n:,} spots, 16x16 FP32, isotropic, VJP of all "
                                    "outputs w.r.t. all pixels",
                        "value": bb.n / (bms * 1e-3), "unit": "spots/s", "ms_per_step": bms,
                        "roofline": {"bound": "hbm", "achieved": nbytes / (bms * 1e-3) / 1e9,
                                     "peak": hbm, "unit": "GB/s",
                                     "frac": nbytes / (bms * 1e-3) / 1e9 / hbm,
                                     "bytes_per_spot": 256 * 8 + 73,
+                                    "traffic": _traffic_from_profile(BWD_PROFILE, BWD_SOURCE),
                                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
-    del bb, fo, gimg
+    return {"backward": out_b}
+
+
+def _extra_serving(args, dev) -> dict:
+    import numpy as np
+    import torch
+    from paper_2106_02045_gb300 import serving, synth
+    out = {}
     # serving: 2048x2048 uint16 frames at 2000 fps, 64 markers, 21x21 ROIs cut on device
     cs = synth.make_camera_stream(args.serving_ring, 64, 2048, 2048, device=dev)
     host = torch.empty(cs.frames.shape, dtype=torch.uint16, pin_memory=True)
@@ -471,6 +506,8 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
+    ap.add_argument("--extras", default="mixed,backward,serving",
+                    help="comma-separated subset of mixed,backward,serving")
     ap.add_argument("--mixed-spots", type=int, default=2_000_000)
     ap.add_argument("--serving-frames", type=int, default=20000)
     ap.add_argument("--serving-warmup", type=int, default=1000)

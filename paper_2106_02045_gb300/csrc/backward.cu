@@ -35,14 +35,18 @@ namespace {
 
 constexpr int kBwdThreads = 128;
 constexpr int kBwdWarps = kBwdThreads / 32;
-constexpr int kGroup = 32;   // spots per warp group (one per lane in phase S)
+constexpr int kGroup = 16;   // spots per warp group: lane j and lane j + 16 serve spot j in phase S
+constexpr int kAhead = 3;    // spots prefetched into L2 ahead of phase A
 constexpr int kNG = 13;      // bilinear data sums G_ab
 constexpr int kGStride = kGroup + 1;
+constexpr int kRedStride = 36;  // reduction row stride (floats): float4 rows on distinct banks
 constexpr int kChunk = 8;    // pixel rows a lane loads before it computes on them
-// per warp: row table [32][8], reduction rows [kNG][32], group table [kNG][kGStride],
-// pass-B row table [32] float2
-constexpr int kGTabFloats = (kNG * kGStride + 1) / 2 * 2;
-constexpr int kBwdWarpFloats = (32 * 8 + kNG * 32 + kGTabFloats + 32 * 2 + 3) / 4 * 4;
+constexpr int kRec = 20;     // per-spot record (floats)
+// per warp: row table [32][8], reduction rows [kNG][kRedStride], group table [kNG][kGStride],
+// spot records [kGroup][kRec], next-group pixel ranges [kGroup] int4, pass-B row table [32] float2
+constexpr int kGTabFloats = (kNG * kGStride + 3) / 4 * 4;
+constexpr int kBwdWarpFloats =
+    32 * 8 + kNG * kRedStride + kGTabFloats + kGroup * kRec + kGroup * 4 + 32 * 2;
 
 struct BwdArgs {
   const void *images;
@@ -58,9 +62,9 @@ struct BwdArgs {
   float *grad;
 };
 
-__device__ __forceinline__ float pix(const BwdArgs &a, int64_t idx) {
-  return a.dtype == FS_U16 ? (float)static_cast<const unsigned short *>(a.images)[idx]
-                           : static_cast<const float *>(a.images)[idx];
+template <typename T>
+__device__ __forceinline__ float ldpix(const T *p) {
+  return (float)__ldg(p);
 }
 
 // bilinear data sums G_ab (slot: (a, b))
@@ -110,45 +114,193 @@ __device__ __forceinline__ void back_step(const float (&M)[6][6], float (&v)[6])
   v[R] = t / M[R][R];
 }
 
-__device__ __forceinline__ float shfl(float v, int j) { return __shfl_sync(0xffffffffu, v, j); }
-__device__ __forceinline__ int shfl(int v, int j) { return __shfl_sync(0xffffffffu, v, j); }
-
-// Prefetch into L2 the pixel range of a spot (whole 128-byte lines; the range is in bounds
-// and every touched line overlaps it).
-__device__ __forceinline__ void prefetch_spot(const BwdArgs &a, int s) {
-  const int W = a.dims[2 * s], H = a.dims[2 * s + 1];
-  const int64_t off = a.offsets[s];
-  if (W < 1 || H < 1 || W > 32 || H > 32 || off < 0 || off + (int64_t)W * H > a.image_elems)
-    return;
-  const int esz = a.dtype == FS_U16 ? 2 : 4;
-  const char *base = static_cast<const char *>(a.images);
-  const uintptr_t lo = reinterpret_cast<uintptr_t>(base + off * esz) & ~uintptr_t(127);
-  const uintptr_t hi = reinterpret_cast<uintptr_t>(base + (off + (int64_t)W * H) * esz);
-  for (uintptr_t p = lo; p < hi; p += 128)
-    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
+// Prefetch into L2 the 128-byte lines of the pixel range [off, off + npx) of a spot: lane l
+// takes line l (and lane 0 line 32, which a misaligned 4 KB range can need). Every touched
+// line overlaps the range.
+template <typename T>
+__device__ __forceinline__ void prefetch_range(const T *img, int64_t off, int npx, int lane) {
+  if (npx <= 0) return;
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(img + off) & ~uintptr_t(127);
+  const uintptr_t hi = reinterpret_cast<uintptr_t>(img + off + npx);
+  const uintptr_t p = lo + 128u * (uintptr_t)lane;
+  if (p < hi) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
+  const uintptr_t q = lo + 128u * 32u;
+  if (lane == 0 && q < hi) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(q));
 }
 
+// The spot's record: geometry and profile (phase A), solution coefficients (phase B).
+struct SpotRec {
+  float x0, y0, ivx, ivy;
+  float sh, rW, al, bp;
+  float vx, vy, vsx, vsy;   // v . K coefficients of the 1-D parts (already times 1/s^2, 1/s^3)
+  float va, vb, cchi, pad;
+  int off_lo, off_hi, whr, nrow;  // whr = W | H << 8 | rows-per-step << 16
+};
+static_assert(sizeof(SpotRec) == kRec * 4, "record size");
+
+// M for q = (x0, y0, sx, sy, alpha, beta) from the 13 data sums and the 1-D moments, the
+// isotropic fold, and the Jacobi-scaled solve M v = u. Returns false for a singular or
+// non-finite system.
+__device__ __forceinline__ bool solve_spot(const float (&G)[kNG], const float (&Ex)[5],
+                                           const float (&Px)[5], const float (&Fy)[5],
+                                           const float (&Qy)[5], float ivx, float ivy, float cx,
+                                           float cy, float al, float bp, int N, bool iso,
+                                           float (&v)[6]) {
+  const float E0 = Ex[0], E1 = Ex[1], E2 = Ex[2], E3 = Ex[3], E4 = Ex[4];
+  const float P0 = Px[0], P1 = Px[1], P2 = Px[2], P3 = Px[3], P4 = Px[4];
+  const float F0 = Fy[0], F1 = Fy[1], F2 = Fy[2], F3 = Fy[3], F4 = Fy[4];
+  const float Q0 = Qy[0], Q1 = Qy[1], Q2 = Qy[2], Q3 = Qy[3], Q4 = Qy[4];
+  // sum d_j d_k (= sum f^2 phi_j phi_k), sum f d_j, sum d_j, sum g' d_j, sum g' h_jk,
+  // sum f h_jk, sum h_jk with phi = (ivx dx, ivy dy, cx dx^2, cy dy^2)
+  float DD[10], FD[4], SD[4], GD[4], GH[10], FH[10], SH[10];
+  DD[0] = ivx * ivx * P2 * Q0;
+  DD[1] = ivx * ivy * P1 * Q1;
+  DD[2] = ivx * cx * P3 * Q0;
+  DD[3] = ivx * cy * P1 * Q2;
+  DD[4] = ivy * ivy * P0 * Q2;
+  DD[5] = ivy * cx * P2 * Q1;
+  DD[6] = ivy * cy * P0 * Q3;
+  DD[7] = cx * cx * P4 * Q0;
+  DD[8] = cx * cy * P2 * Q2;
+  DD[9] = cy * cy * P0 * Q4;
+  FD[0] = ivx * P1 * Q0;
+  FD[1] = ivy * P0 * Q1;
+  FD[2] = cx * P2 * Q0;
+  FD[3] = cy * P0 * Q2;
+  SD[0] = ivx * E1 * F0;
+  SD[1] = ivy * E0 * F1;
+  SD[2] = cx * E2 * F0;
+  SD[3] = cy * E0 * F2;
+  GD[0] = ivx * G[G10];
+  GD[1] = ivy * G[G01];
+  GD[2] = cx * G[G20];
+  GD[3] = cy * G[G02];
+  GH[0] = ivx * ivx * G[G20] - ivx * G[G00];
+  FH[0] = ivx * ivx * P2 * Q0 - ivx * P0 * Q0;
+  SH[0] = ivx * ivx * E2 * F0 - ivx * E0 * F0;
+  GH[1] = ivx * ivy * G[G11];
+  FH[1] = ivx * ivy * P1 * Q1;
+  SH[1] = ivx * ivy * E1 * F1;
+  GH[2] = ivx * cx * G[G30] - 2.f * cx * G[G10];
+  FH[2] = ivx * cx * P3 * Q0 - 2.f * cx * P1 * Q0;
+  SH[2] = ivx * cx * E3 * F0 - 2.f * cx * E1 * F0;
+  GH[3] = ivx * cy * G[G12];
+  FH[3] = ivx * cy * P1 * Q2;
+  SH[3] = ivx * cy * E1 * F2;
+  GH[4] = ivy * ivy * G[G02] - ivy * G[G00];
+  FH[4] = ivy * ivy * P0 * Q2 - ivy * P0 * Q0;
+  SH[4] = ivy * ivy * E0 * F2 - ivy * E0 * F0;
+  GH[5] = ivy * cx * G[G21];
+  FH[5] = ivy * cx * P2 * Q1;
+  SH[5] = ivy * cx * E2 * F1;
+  GH[6] = ivy * cy * G[G03] - 2.f * cy * G[G01];
+  FH[6] = ivy * cy * P0 * Q3 - 2.f * cy * P0 * Q1;
+  SH[6] = ivy * cy * E0 * F3 - 2.f * cy * E0 * F1;
+  GH[7] = cx * cx * G[G40] - 3.f * ivx * ivx * G[G20];
+  FH[7] = cx * cx * P4 * Q0 - 3.f * ivx * ivx * P2 * Q0;
+  SH[7] = cx * cx * E4 * F0 - 3.f * ivx * ivx * E2 * F0;
+  GH[8] = cx * cy * G[G22];
+  FH[8] = cx * cy * P2 * Q2;
+  SH[8] = cx * cy * E2 * F2;
+  GH[9] = cy * cy * G[G04] - 3.f * ivy * ivy * G[G02];
+  FH[9] = cy * cy * P0 * Q4 - 3.f * ivy * ivy * P0 * Q2;
+  SH[9] = cy * cy * E0 * F4 - 3.f * ivy * ivy * E0 * F2;
+  float M[6][6];
+  {
+    int t = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = j; k < 4; ++k, ++t) {
+        const float rh = GH[t] - al * FH[t] - bp * SH[t];  // sum r h_jk
+        M[j][k] = M[k][j] = al * (al * DD[t] - rh);
+      }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float rd = GD[j] - al * FD[j] - bp * SD[j];  // sum r d_j
+      M[j][4] = M[4][j] = al * FD[j] - rd;
+      M[j][5] = M[5][j] = al * SD[j];
+    }
+  }
+  M[4][4] = P0 * Q0;
+  M[4][5] = M[5][4] = E0 * F0;
+  M[5][5] = (float)N;
+  if (iso) {  // sigma_x = sigma_y = sigma: merge row/column 3 into 2, leave 3 as identity
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[2][k] += M[3][k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[k][2] += M[k][3];
+    v[2] += v[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[3][k] = M[k][3] = 0.f;
+    M[3][3] = 1.f;
+    v[3] = 0.f;
+  }
+  // Jacobi scaling, then Gaussian elimination with partial pivoting
+  bool ok = true;
+  float sc[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    ok = ok && M[j][j] > 0.f;
+    sc[j] = M[j][j] > 0.f ? rsqrtf(M[j][j]) : 1.f;
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[j][k] *= sc[j] * sc[k];
+    v[j] *= sc[j];
+  }
+  elim_step<0>(M, v, ok);
+  elim_step<1>(M, v, ok);
+  elim_step<2>(M, v, ok);
+  elim_step<3>(M, v, ok);
+  elim_step<4>(M, v, ok);
+  elim_step<5>(M, v, ok);
+  back_step<5>(M, v);
+  back_step<4>(M, v);
+  back_step<3>(M, v);
+  back_step<2>(M, v);
+  back_step<1>(M, v);
+  back_step<0>(M, v);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    v[j] *= sc[j];
+    ok = ok && isfinite(v[j]);
+  }
+  return ok;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
   __shared__ float4 sm4[kBwdWarps * kBwdWarpFloats / 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T *const img = static_cast<const T *>(a.images);
   float *const rowt = reinterpret_cast<float *>(sm4) + warp * kBwdWarpFloats;  // [32][8]
-  float *const red = rowt + 32 * 8;                        // [kNG][32]
-  float *const gtab = red + kNG * 32;                      // [kNG][kGStride]
-  float2 *const rowb = reinterpret_cast<float2 *>(gtab + kGTabFloats);  // [32]
+  float *const red = rowt + 32 * 8;                                            // [kNG][36]
+  float *const gtab = red + kNG * kRedStride;                                  // [kNG][17]
+  SpotRec *const rec = reinterpret_cast<SpotRec *>(gtab + kGTabFloats);        // [kGroup]
+  int4 *const nxt = reinterpret_cast<int4 *>(rec + kGroup);  // next group: offset, pixels
+  float2 *const rowb = reinterpret_cast<float2 *>(nxt + kGroup);               // [32]
   const int ngroups = (a.n + kGroup - 1) / kGroup;
   const int gstride = gridDim.x * kBwdWarps;
+  const int jl = lane & (kGroup - 1);  // the group spot this lane serves in phases 0 and S
+  const bool ylane = lane >= kGroup;    // phase S: the y moments of spot jl
   int g = blockIdx.x * kBwdWarps + warp;
-  if (g < ngroups && g * kGroup + lane < a.n) prefetch_spot(a, g * kGroup + lane);
+  if (g < ngroups && lane < kAhead && g * kGroup + lane < a.n) {
+    const int s = g * kGroup + lane;
+    const int W = a.dims[2 * s], H = a.dims[2 * s + 1];
+    const int64_t off = a.offsets[s];
+    if (W >= 1 && H >= 1 && W <= 32 && H <= 32 && off >= 0 &&
+        off + (int64_t)W * H <= a.image_elems)
+      for (int l = 0; l < 32; ++l) prefetch_range(img, off, W * H, l);
+  }
   for (; g < ngroups; g += gstride) {
     const int s0 = g * kGroup;
     const int ns = min(kGroup, a.n - s0);
-    {
-      const int sn = (g + gstride) * kGroup + lane;
-      if (g + gstride < ngroups && sn < a.n) prefetch_spot(a, sn);
-    }
-    // ---- lane j holds spot s0 + j
-    const int s = s0 + lane;
-    const bool have = lane < ns;
+    // ---- phase 0: lanes j and j + 16 read spot s0 + j; lanes 16.. also read the pixel range
+    // of spot j of this warp's next group (for the prefetch)
+    const int s = s0 + jl;
+    const bool have = jl < ns;
     const int W = have ? a.dims[2 * s] : 0, H = have ? a.dims[2 * s + 1] : 0;
     const int m = have ? a.model[s] : -1;
     const int64_t off = have ? a.offsets[s] : 0;
@@ -172,19 +324,53 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
     const float ivx = 1.f / (sx * sx), ivy = 1.f / (sy * sy);
     const float sh = rintf(be), bp = be - sh;
     const int rps = valid ? 32 / W : 1;
-    const float rW = valid ? 1.f / (float)W : 1.f;
-    const int nrow = valid ? (H + rps - 1) / rps : 0;  // row steps of the pixel passes
-    const unsigned conv_mask = __ballot_sync(0xffffffffu, conv);
-    const unsigned valid_mask = __ballot_sync(0xffffffffu, valid);
+    if (!ylane) {
+      SpotRec &r = rec[jl];
+      *reinterpret_cast<float4 *>(&r.x0) = make_float4(x0, y0, ivx, ivy);
+      *reinterpret_cast<float4 *>(&r.sh) = make_float4(sh, valid ? 1.f / (float)W : 1.f, al, bp);
+      *reinterpret_cast<int4 *>(&r.off_lo) =
+          make_int4((int)(off & 0xffffffff), (int)(off >> 32), W | (H << 8) | (rps << 16),
+                    valid ? (H + rps - 1) / rps : 0);
+    } else {
+      int4 rng = make_int4(0, 0, 0, 0);
+      if (g + gstride < ngroups) {
+        const int sn = (g + gstride) * kGroup + jl;
+        if (sn < a.n) {
+          const int Wn = a.dims[2 * sn], Hn = a.dims[2 * sn + 1];
+          const int64_t on = a.offsets[sn];
+          if (Wn >= 1 && Hn >= 1 && Wn <= 32 && Hn <= 32 && on >= 0 &&
+              on + (int64_t)Wn * Hn <= a.image_elems)
+            rng = make_int4((int)(on & 0xffffffff), (int)(on >> 32), Wn * Hn, 0);
+        }
+      }
+      nxt[jl] = rng;
+    }
+    const unsigned conv_mask = __ballot_sync(0xffffffffu, conv) & 0xffffu;
+    const unsigned valid_mask = __ballot_sync(0xffffffffu, valid) & 0xffffu;
+    __syncwarp();
 
     // ---- phase A: G_ab of each converged spot into gtab[k][j]
     for (int j = 0; j < ns; ++j) {
+      {  // prefetch spot j + kAhead (this group's record, else the next group's range)
+        const int t = j + kAhead;
+        if (t < ns) {
+          const int4 o = *reinterpret_cast<const int4 *>(&rec[t].off_lo);
+          const int64_t ot = (int64_t)(((uint64_t)(uint32_t)o.y << 32) | (uint32_t)o.x);
+          if ((valid_mask >> t) & 1u)
+            prefetch_range(img, ot, (o.z & 0xff) * ((o.z >> 8) & 0xff), lane);
+        } else if (t - kGroup >= 0 && t - kGroup < kGroup) {
+          const int4 r4 = nxt[t - kGroup];
+          prefetch_range(img, (int64_t)(((uint64_t)(uint32_t)r4.y << 32) | (uint32_t)r4.x), r4.z,
+                         lane);
+        }
+      }
       if (!((conv_mask >> j) & 1u)) continue;
-      const int Wj = shfl(W, j), Hj = shfl(H, j), rpsj = shfl(rps, j), nrj = shfl(nrow, j);
-      const int olo = shfl((int)(off & 0xffffffff), j), ohi = shfl((int)(off >> 32), j);
-      const int64_t offj = (int64_t)(((uint64_t)(uint32_t)ohi << 32) | (uint32_t)olo);
-      const float x0j = shfl(x0, j), y0j = shfl(y0, j), ivxj = shfl(ivx, j), ivyj = shfl(ivy, j);
-      const float shj = shfl(sh, j), rWj = shfl(rW, j);
+      const float4 ra = *reinterpret_cast<const float4 *>(&rec[j].x0);
+      const float4 rb = *reinterpret_cast<const float4 *>(&rec[j].sh);
+      const int4 rc = *reinterpret_cast<const int4 *>(&rec[j].off_lo);
+      const float x0j = ra.x, y0j = ra.y, ivxj = ra.z, ivyj = ra.w, shj = rb.x, rWj = rb.y;
+      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = rc.z >> 16, nrj = rc.w;
+      const T *const pj = img + (int64_t)(((uint64_t)(uint32_t)rc.y << 32) | (uint32_t)rc.x);
       // row table: e_y dy^b, b = 0..4 (zero beyond the ROI)
       {
         const float dy = (float)lane - y0j;
@@ -203,7 +389,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
           const int y = yo + (t0 + u) * rpsj;
-          gv[u] = plane && y < Hj ? pix(a, offj + (int64_t)y * Wj + xl) - shj : 0.f;
+          gv[u] = plane && y < Hj ? ldpix(pj + (y * Wj + xl)) - shj : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
@@ -229,250 +415,139 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
         const float dx = (float)lane - x0j;
         const float p0 = lane < Wj ? __expf(-0.5f * dx * dx * ivxj) : 0.f;
         const float p1 = p0 * dx, p2 = p1 * dx, p3 = p2 * dx, p4 = p3 * dx;
-        red[G00 * 32 + lane] = p0 * c0;
-        red[G10 * 32 + lane] = p1 * c0;
-        red[G01 * 32 + lane] = p0 * c1;
-        red[G20 * 32 + lane] = p2 * c0;
-        red[G02 * 32 + lane] = p0 * c2;
-        red[G11 * 32 + lane] = p1 * c1;
-        red[G30 * 32 + lane] = p3 * c0;
-        red[G03 * 32 + lane] = p0 * c3;
-        red[G12 * 32 + lane] = p1 * c2;
-        red[G21 * 32 + lane] = p2 * c1;
-        red[G40 * 32 + lane] = p4 * c0;
-        red[G22 * 32 + lane] = p2 * c2;
-        red[G04 * 32 + lane] = p0 * c4;
+        red[G00 * kRedStride + lane] = p0 * c0;
+        red[G10 * kRedStride + lane] = p1 * c0;
+        red[G01 * kRedStride + lane] = p0 * c1;
+        red[G20 * kRedStride + lane] = p2 * c0;
+        red[G02 * kRedStride + lane] = p0 * c2;
+        red[G11 * kRedStride + lane] = p1 * c1;
+        red[G30 * kRedStride + lane] = p3 * c0;
+        red[G03 * kRedStride + lane] = p0 * c3;
+        red[G12 * kRedStride + lane] = p1 * c2;
+        red[G21 * kRedStride + lane] = p2 * c1;
+        red[G40 * kRedStride + lane] = p4 * c0;
+        red[G22 * kRedStride + lane] = p2 * c2;
+        red[G04 * kRedStride + lane] = p0 * c4;
       }
       __syncwarp();
       if (lane < kNG) {
-        const float4 *r = reinterpret_cast<const float4 *>(red + lane * 32);
-        float q[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float4 w = r[i];
-          q[i] = (w.x + w.y) + (w.z + w.w);
+        const float4 *r = reinterpret_cast<const float4 *>(red + lane * kRedStride);
+        const int nq = (Wj + 3) >> 2;
+        float q0 = 0.f, q1 = 0.f;
+        int i = 0;
+        for (; i + 1 < nq; i += 2) {
+          const float4 w0 = r[i], w1 = r[i + 1];
+          q0 += (w0.x + w0.y) + (w0.z + w0.w);
+          q1 += (w1.x + w1.y) + (w1.z + w1.w);
         }
-        gtab[lane * kGStride + j] =
-            ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
+        if (i < nq) {
+          const float4 w0 = r[i];
+          q0 += (w0.x + w0.y) + (w0.z + w0.w);
+        }
+        gtab[lane * kGStride + j] = q0 + q1;
       }
       __syncwarp();
     }
 
-    // ---- phase S: lane j builds M for its spot and solves M v = u
+    // ---- phase S: lane j (x moments, the solve) and lane j + 16 (y moments) for spot j
     float vx = 0.f, vy = 0.f, vsx = 0.f, vsy = 0.f, va = 0.f, vb = 0.f, cchi = 0.f;
     bool ok = false;
-    if (conv) {
-      const float cx = ivx / sx, cy = ivy / sy;
-      float E0 = 0.f, E1 = 0.f, E2 = 0.f, E3 = 0.f, E4 = 0.f;
-      float P0 = 0.f, P1 = 0.f, P2 = 0.f, P3 = 0.f, P4 = 0.f;
-      for (int x = 0; x < W; ++x) {
-        const float d = (float)x - x0;
-        const float e = __expf(-0.5f * d * d * ivx), ee = e * e;
-        const float d2 = d * d;
-        E0 += e;
-        E1 = fmaf(e, d, E1);
-        E2 = fmaf(e, d2, E2);
-        E3 = fmaf(e * d, d2, E3);
-        E4 = fmaf(e * d2, d2, E4);
-        P0 += ee;
-        P1 = fmaf(ee, d, P1);
-        P2 = fmaf(ee, d2, P2);
-        P3 = fmaf(ee * d, d2, P3);
-        P4 = fmaf(ee * d2, d2, P4);
+    {
+      const int nA = ylane ? H : W;
+      const float cA = ylane ? y0 : x0, ivA = ylane ? ivy : ivx;
+      float Ex[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Px[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      if (conv)
+        for (int x = 0; x < nA; ++x) {
+          const float d = (float)x - cA;
+          const float e = __expf(-0.5f * d * d * ivA), ee = e * e;
+          const float d2 = d * d;
+          Ex[0] += e;
+          Ex[1] = fmaf(e, d, Ex[1]);
+          Ex[2] = fmaf(e, d2, Ex[2]);
+          Ex[3] = fmaf(e * d, d2, Ex[3]);
+          Ex[4] = fmaf(e * d2, d2, Ex[4]);
+          Px[0] += ee;
+          Px[1] = fmaf(ee, d, Px[1]);
+          Px[2] = fmaf(ee, d2, Px[2]);
+          Px[3] = fmaf(ee * d, d2, Px[3]);
+          Px[4] = fmaf(ee * d2, d2, Px[4]);
+        }
+      float Fy[5], Qy[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        Fy[k] = __shfl_down_sync(0xffffffffu, Ex[k], kGroup);
+        Qy[k] = __shfl_down_sync(0xffffffffu, Px[k], kGroup);
       }
-      float F0 = 0.f, F1 = 0.f, F2 = 0.f, F3 = 0.f, F4 = 0.f;
-      float Q0 = 0.f, Q1 = 0.f, Q2 = 0.f, Q3 = 0.f, Q4 = 0.f;
-      for (int y = 0; y < H; ++y) {
-        const float d = (float)y - y0;
-        const float e = __expf(-0.5f * d * d * ivy), ee = e * e;
-        const float d2 = d * d;
-        F0 += e;
-        F1 = fmaf(e, d, F1);
-        F2 = fmaf(e, d2, F2);
-        F3 = fmaf(e * d, d2, F3);
-        F4 = fmaf(e * d2, d2, F4);
-        Q0 += ee;
-        Q1 = fmaf(ee, d, Q1);
-        Q2 = fmaf(ee, d2, Q2);
-        Q3 = fmaf(ee * d, d2, Q3);
-        Q4 = fmaf(ee * d2, d2, Q4);
-      }
-      float G[kNG];
+      if (conv && !ylane) {
+        float G[kNG];
 #pragma unroll
-      for (int k = 0; k < kNG; ++k) G[k] = gtab[k * kGStride + lane];
-      // sum d_j d_k (= sum f^2 phi_j phi_k), sum f d_j, sum d_j, sum g' d_j, sum g' h_jk,
-      // sum f h_jk, sum h_jk with phi = (ivx dx, ivy dy, cx dx^2, cy dy^2)
-      float DD[10], FD[4], SD[4], GD[4], GH[10], FH[10], SH[10];
-      DD[0] = ivx * ivx * P2 * Q0;
-      DD[1] = ivx * ivy * P1 * Q1;
-      DD[2] = ivx * cx * P3 * Q0;
-      DD[3] = ivx * cy * P1 * Q2;
-      DD[4] = ivy * ivy * P0 * Q2;
-      DD[5] = ivy * cx * P2 * Q1;
-      DD[6] = ivy * cy * P0 * Q3;
-      DD[7] = cx * cx * P4 * Q0;
-      DD[8] = cx * cy * P2 * Q2;
-      DD[9] = cy * cy * P0 * Q4;
-      FD[0] = ivx * P1 * Q0;
-      FD[1] = ivy * P0 * Q1;
-      FD[2] = cx * P2 * Q0;
-      FD[3] = cy * P0 * Q2;
-      SD[0] = ivx * E1 * F0;
-      SD[1] = ivy * E0 * F1;
-      SD[2] = cx * E2 * F0;
-      SD[3] = cy * E0 * F2;
-      GD[0] = ivx * G[G10];
-      GD[1] = ivy * G[G01];
-      GD[2] = cx * G[G20];
-      GD[3] = cy * G[G02];
-      GH[0] = ivx * ivx * G[G20] - ivx * G[G00];
-      FH[0] = ivx * ivx * P2 * Q0 - ivx * P0 * Q0;
-      SH[0] = ivx * ivx * E2 * F0 - ivx * E0 * F0;
-      GH[1] = ivx * ivy * G[G11];
-      FH[1] = ivx * ivy * P1 * Q1;
-      SH[1] = ivx * ivy * E1 * F1;
-      GH[2] = ivx * cx * G[G30] - 2.f * cx * G[G10];
-      FH[2] = ivx * cx * P3 * Q0 - 2.f * cx * P1 * Q0;
-      SH[2] = ivx * cx * E3 * F0 - 2.f * cx * E1 * F0;
-      GH[3] = ivx * cy * G[G12];
-      FH[3] = ivx * cy * P1 * Q2;
-      SH[3] = ivx * cy * E1 * F2;
-      GH[4] = ivy * ivy * G[G02] - ivy * G[G00];
-      FH[4] = ivy * ivy * P0 * Q2 - ivy * P0 * Q0;
-      SH[4] = ivy * ivy * E0 * F2 - ivy * E0 * F0;
-      GH[5] = ivy * cx * G[G21];
-      FH[5] = ivy * cx * P2 * Q1;
-      SH[5] = ivy * cx * E2 * F1;
-      GH[6] = ivy * cy * G[G03] - 2.f * cy * G[G01];
-      FH[6] = ivy * cy * P0 * Q3 - 2.f * cy * P0 * Q1;
-      SH[6] = ivy * cy * E0 * F3 - 2.f * cy * E0 * F1;
-      GH[7] = cx * cx * G[G40] - 3.f * ivx * ivx * G[G20];
-      FH[7] = cx * cx * P4 * Q0 - 3.f * ivx * ivx * P2 * Q0;
-      SH[7] = cx * cx * E4 * F0 - 3.f * ivx * ivx * E2 * F0;
-      GH[8] = cx * cy * G[G22];
-      FH[8] = cx * cy * P2 * Q2;
-      SH[8] = cx * cy * E2 * F2;
-      GH[9] = cy * cy * G[G04] - 3.f * ivy * ivy * G[G02];
-      FH[9] = cy * cy * P0 * Q4 - 3.f * ivy * ivy * P0 * Q2;
-      SH[9] = cy * cy * E0 * F4 - 3.f * ivy * ivy * E0 * F2;
-      float M[6][6], v[6];
-      {
-        int t = 0;
+        for (int k = 0; k < kNG; ++k) G[k] = gtab[k * kGStride + jl];
+        const float cx = ivx / sx, cy = ivy / sy;
+        float v[6];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int k = j; k < 4; ++k, ++t) {
-            const float rh = GH[t] - al * FH[t] - bp * SH[t];  // sum r h_jk
-            M[j][k] = M[k][j] = al * (al * DD[t] - rh);
-          }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float rd = GD[j] - al * FD[j] - bp * SD[j];  // sum r d_j
-          M[j][4] = M[4][j] = al * FD[j] - rd;
-          M[j][5] = M[5][j] = al * SD[j];
+        for (int k = 0; k < 4; ++k) v[k] = a.gp ? a.gp[4 * s + k] : 0.f;
+        v[4] = a.ga ? a.ga[s] : 0.f;
+        v[5] = a.gb ? a.gb[s] : 0.f;
+        const float uc = a.gc ? a.gc[s] : 0.f;
+        ok = solve_spot(G, Ex, Px, Fy, Qy, ivx, ivy, cx, cy, al, bp, W * H, iso, v);
+        // (vx, vy, vsx, vsy, va, vb) as coefficients of the 1-D parts; the isotropic sigma
+        // moves both widths
+        if (ok) {
+          vx = v[0] * ivx;
+          vy = v[1] * ivy;
+          vsx = v[2] * cx;
+          vsy = (iso ? v[2] : v[3]) * cy;
+          va = v[4];
+          vb = v[5];
+          cchi = 2.f * uc / (float)(W * H - P - 2);
         }
       }
-      M[4][4] = P0 * Q0;
-      M[4][5] = M[5][4] = E0 * F0;
-      M[5][5] = (float)(W * H);
-      // upstream in (x0, y0, sx, sy, alpha, beta) order; the isotropic sigma is reported in
-      // slots 2 and 3, so both feed its gradient
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = a.gp ? a.gp[4 * s + j] : 0.f;
-      v[4] = a.ga ? a.ga[s] : 0.f;
-      v[5] = a.gb ? a.gb[s] : 0.f;
-      const float uc = a.gc ? a.gc[s] : 0.f;
-      if (iso) {  // sigma_x = sigma_y = sigma: merge row/column 3 into 2, leave 3 as identity
-#pragma unroll
-        for (int k = 0; k < 6; ++k) M[2][k] += M[3][k];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) M[k][2] += M[k][3];
-        v[2] += v[3];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) M[3][k] = M[k][3] = 0.f;
-        M[3][3] = 1.f;
-        v[3] = 0.f;
-      }
-      // Jacobi scaling, then Gaussian elimination with partial pivoting
-      ok = true;
-      float sc[6];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        ok = ok && M[j][j] > 0.f;
-        sc[j] = M[j][j] > 0.f ? rsqrtf(M[j][j]) : 1.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) M[j][k] *= sc[j] * sc[k];
-        v[j] *= sc[j];
-      }
-      elim_step<0>(M, v, ok);
-      elim_step<1>(M, v, ok);
-      elim_step<2>(M, v, ok);
-      elim_step<3>(M, v, ok);
-      elim_step<4>(M, v, ok);
-      elim_step<5>(M, v, ok);
-      back_step<5>(M, v);
-      back_step<4>(M, v);
-      back_step<3>(M, v);
-      back_step<2>(M, v);
-      back_step<1>(M, v);
-      back_step<0>(M, v);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        v[j] *= sc[j];
-        ok = ok && isfinite(v[j]);
-      }
-      // (vx, vy, vsx, vsy, va, vb) as coefficients of the 1-D parts; the isotropic sigma
-      // moves both widths
-      if (ok) {
-        vx = v[0] * ivx;
-        vy = v[1] * ivy;
-        vsx = v[2] * cx;
-        vsy = (iso ? v[2] : v[3]) * cy;
-        va = v[4];
-        vb = v[5];
-        cchi = 2.f * uc / (float)(W * H - P - 2);
-      }
     }
-    const unsigned ok_mask = __ballot_sync(0xffffffffu, ok);
+    if (!ylane) {
+      SpotRec &r = rec[jl];
+      *reinterpret_cast<float4 *>(&r.vx) = make_float4(vx, vy, vsx, vsy);
+      *reinterpret_cast<float4 *>(&r.va) = make_float4(va, vb, cchi, 0.f);
+    }
+    const unsigned ok_mask = __ballot_sync(0xffffffffu, ok) & 0xffffu;
+    __syncwarp();
 
     // ---- phase B: grad_g = e_x e_y (alpha (A(x) + B(y)) + va) + vb + cchi (g' - alpha f - bp)
     for (int j = 0; j < ns; ++j) {
       if (!((valid_mask >> j) & 1u)) continue;
-      const bool okj = (ok_mask >> j) & 1u;
-      const int Wj = shfl(W, j), Hj = shfl(H, j), rpsj = shfl(rps, j), nrj = shfl(nrow, j);
-      const int olo = shfl((int)(off & 0xffffffff), j), ohi = shfl((int)(off >> 32), j);
-      const int64_t offj = (int64_t)(((uint64_t)(uint32_t)ohi << 32) | (uint32_t)olo);
-      const float rWj = shfl(rW, j);
-      const int yo = (int)(((float)lane + 0.5f) * rWj);
+      const int4 rc = *reinterpret_cast<const int4 *>(&rec[j].off_lo);
+      const float4 rb = *reinterpret_cast<const float4 *>(&rec[j].sh);
+      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = rc.z >> 16, nrj = rc.w;
+      const int64_t offj = (int64_t)(((uint64_t)(uint32_t)rc.y << 32) | (uint32_t)rc.x);
+      const T *const pj = img + offj;
+      float *const gj = a.grad + offj;
+      const int yo = (int)(((float)lane + 0.5f) * rb.y);
       const int xl = lane - yo * Wj;
       const bool plane = yo < rpsj;
-      if (!okj) {  // no gradient through fits that did not converge
+      if (!((ok_mask >> j) & 1u)) {  // no gradient through fits that did not converge
         if (plane)
-          for (int y = yo; y < Hj; y += rpsj) a.grad[offj + (int64_t)y * Wj + xl] = 0.f;
+          for (int y = yo; y < Hj; y += rpsj) gj[y * Wj + xl] = 0.f;
         continue;
       }
-      const float x0j = shfl(x0, j), y0j = shfl(y0, j), ivxj = shfl(ivx, j), ivyj = shfl(ivy, j);
-      const float alj = shfl(al, j), shj = shfl(sh, j), bpj = shfl(bp, j);
-      const float vxj = shfl(vx, j), vyj = shfl(vy, j), vsxj = shfl(vsx, j), vsyj = shfl(vsy, j);
-      const float vaj = shfl(va, j), vbj = shfl(vb, j), ccj = shfl(cchi, j);
+      const float4 ra = *reinterpret_cast<const float4 *>(&rec[j].x0);
+      const float4 rv = *reinterpret_cast<const float4 *>(&rec[j].vx);
+      const float4 rw = *reinterpret_cast<const float4 *>(&rec[j].va);
+      const float shj = rb.x, alj = rb.z, bpj = rb.w;
+      const float vaj = rw.x, vbj = rw.y, ccj = rw.z;
       {
-        const float dy = (float)lane - y0j;
-        const float e = lane < Hj ? __expf(-0.5f * dy * dy * ivyj) : 0.f;
-        rowb[lane] = make_float2(e, dy * fmaf(vsyj, dy, vyj));
+        const float dy = (float)lane - ra.y;
+        const float e = lane < Hj ? __expf(-0.5f * dy * dy * ra.w) : 0.f;
+        rowb[lane] = make_float2(e, dy * fmaf(rv.w, dy, rv.y));
       }
       __syncwarp();
-      const float dx = (float)xl - x0j;
-      const float ex = __expf(-0.5f * dx * dx * ivxj);
-      const float Ax = dx * fmaf(vsxj, dx, vxj);
+      const float dx = (float)xl - ra.x;
+      const float ex = __expf(-0.5f * dx * dx * ra.z);
+      const float Ax = dx * fmaf(rv.z, dx, rv.x);
       for (int t0 = 0; t0 < nrj; t0 += kChunk) {
         float gv[kChunk];
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
           const int y = yo + (t0 + u) * rpsj;
-          gv[u] = plane && y < Hj ? pix(a, offj + (int64_t)y * Wj + xl) - shj : 0.f;
+          gv[u] = plane && y < Hj ? ldpix(pj + (y * Wj + xl)) - shj : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
@@ -481,12 +556,13 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
             const float2 eb = rowb[y];
             const float f = ex * eb.x;
             const float r = gv[u] - fmaf(alj, f, bpj);
-            a.grad[offj + (int64_t)y * Wj + xl] = fmaf(f, fmaf(alj, Ax + eb.y, vaj), vbj) + ccj * r;
+            gj[y * Wj + xl] = fmaf(f, fmaf(alj, Ax + eb.y, vaj), vbj) + ccj * r;
           }
         }
       }
       __syncwarp();
     }
+    __syncwarp();
   }
 }
 
@@ -530,11 +606,18 @@ extern "C" int fit_spots_backward(const void *images, int dtype, int64_t image_e
   const int64_t groups = (n + kGroup - 1) / kGroup;
   int64_t blocks = (groups + warps_per_block - 1) / warps_per_block;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel, kBwdThreads, 0);
+  e = dtype == FS_U16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, backward_kernel<unsigned short>, kBwdThreads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, backward_kernel<float>, kBwdThreads, 0);
   if (e != cudaSuccess) return FS_ERR_CUDA;
   const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   if (blocks > cap) blocks = cap;
-  backward_kernel<<<(int)blocks, kBwdThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+  if (dtype == FS_U16)
+    backward_kernel<unsigned short>
+        <<<(int)blocks, kBwdThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+  else
+    backward_kernel<float><<<(int)blocks, kBwdThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
   e = cudaGetLastError();
   return e == cudaSuccess ? FS_OK : FS_ERR_CUDA;
 }

@@ -114,18 +114,53 @@ __device__ __forceinline__ void back_step(const float (&M)[6][6], float (&v)[6])
   v[R] = t / M[R][R];
 }
 
-// Prefetch into L2 the 128-byte lines of the pixel range [off, off + npx) of a spot: lane l
-// takes line l (and lane 0 line 32, which a misaligned 4 KB range can need). Every touched
-// line overlaps the range.
+// Prefetch into L2 the pixel range [off, off + npx) of a spot with one bulk prefetch, the
+// range widened to 16-byte boundaries (which stay inside the pages the range touches).
 template <typename T>
-__device__ __forceinline__ void prefetch_range(const T *img, int64_t off, int npx, int lane) {
+__device__ __forceinline__ void prefetch_range(const T *img, int64_t off, int npx) {
   if (npx <= 0) return;
-  const uintptr_t lo = reinterpret_cast<uintptr_t>(img + off) & ~uintptr_t(127);
-  const uintptr_t hi = reinterpret_cast<uintptr_t>(img + off + npx);
-  const uintptr_t p = lo + 128u * (uintptr_t)lane;
-  if (p < hi) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
-  const uintptr_t q = lo + 128u * 32u;
-  if (lane == 0 && q < hi) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(q));
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(img + off) & ~uintptr_t(15);
+  const uintptr_t hi = (reinterpret_cast<uintptr_t>(img + off + npx) + 15) & ~uintptr_t(15);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo))
+               : "memory");
+}
+
+// Phase A rows of one lane: c_b += g' e_y dy^b over kChunk rows starting at p (pixels) and
+// rt (row table), rows `step` pixels and `rs` table floats apart; with kPred only the first
+// `nleft` rows count.
+template <typename T, bool kPred>
+__device__ __forceinline__ void rows_a(const T *p, int step, const float *rt, int rs, int nleft,
+                                       float sh, float (&c)[5]) {
+  float gv[kChunk];
+#pragma unroll
+  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * step) - sh : 0.f;
+#pragma unroll
+  for (int u = 0; u < kChunk; ++u) {
+    const float *r = rt + (kPred ? min(u, max(nleft - 1, 0)) : u) * rs;
+    const float4 r4 = *reinterpret_cast<const float4 *>(r);
+    const float r5 = r[4];
+    c[0] = fmaf(gv[u], r4.x, c[0]);
+    c[1] = fmaf(gv[u], r4.y, c[1]);
+    c[2] = fmaf(gv[u], r4.z, c[2]);
+    c[3] = fmaf(gv[u], r4.w, c[3]);
+    c[4] = fmaf(gv[u], r5, c[4]);
+  }
+}
+
+// Phase B rows of one lane: grad = e_x e_y (K1 + alpha B(y)) + u_chi g + K2 with the row
+// table rb = (e_y, alpha B(y)); same row addressing as rows_a.
+template <typename T, bool kPred>
+__device__ __forceinline__ void rows_b(const T *p, float *q, int step, const float2 *rb, int rs,
+                                       int nleft, float ex, float K1, float cc, float K2) {
+  float gv[kChunk];
+#pragma unroll
+  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * step) : 0.f;
+#pragma unroll
+  for (int u = 0; u < kChunk; ++u)
+    if (!kPred || u < nleft) {
+      const float2 eb = rb[u * rs];
+      q[u * step] = fmaf(ex * eb.x, K1 + eb.y, fmaf(cc, gv[u], K2));
+    }
 }
 
 // The spot's record: geometry and profile (phase A), solution coefficients (phase B).
@@ -134,7 +169,7 @@ struct SpotRec {
   float sh, rW, al, bp;
   float vx, vy, vsx, vsy;   // v . K coefficients of the 1-D parts (already times 1/s^2, 1/s^3)
   float va, vb, cchi, pad;
-  int off_lo, off_hi, whr, nrow;  // whr = W | H << 8 | rows-per-step << 16
+  int off_lo, off_hi, whr, nrow;  // whr = W | H << 8 | rows-per-step << 16 | full << 24
 };
 static_assert(sizeof(SpotRec) == kRec * 4, "record size");
 
@@ -271,7 +306,7 @@ __device__ __forceinline__ bool solve_spot(const float (&G)[kNG], const float (&
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
   __shared__ float4 sm4[kBwdWarps * kBwdWarpFloats / 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T *const img = static_cast<const T *>(a.images);
@@ -292,7 +327,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
     const int64_t off = a.offsets[s];
     if (W >= 1 && H >= 1 && W <= 32 && H <= 32 && off >= 0 &&
         off + (int64_t)W * H <= a.image_elems)
-      for (int l = 0; l < 32; ++l) prefetch_range(img, off, W * H, l);
+      prefetch_range(img, off, W * H);
   }
   for (; g < ngroups; g += gstride) {
     const int s0 = g * kGroup;
@@ -324,12 +359,15 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
     const float ivx = 1.f / (sx * sx), ivy = 1.f / (sy * sy);
     const float sh = rintf(be), bp = be - sh;
     const int rps = valid ? 32 / W : 1;
+    // every lane has the same rows: a row step covers 32 pixels and H is a multiple of it
+    const bool full = valid && rps * W == 32 && H % rps == 0;
     if (!ylane) {
       SpotRec &r = rec[jl];
       *reinterpret_cast<float4 *>(&r.x0) = make_float4(x0, y0, ivx, ivy);
       *reinterpret_cast<float4 *>(&r.sh) = make_float4(sh, valid ? 1.f / (float)W : 1.f, al, bp);
       *reinterpret_cast<int4 *>(&r.off_lo) =
-          make_int4((int)(off & 0xffffffff), (int)(off >> 32), W | (H << 8) | (rps << 16),
+          make_int4((int)(off & 0xffffffff), (int)(off >> 32),
+                    W | (H << 8) | (rps << 16) | ((int)full << 24),
                     valid ? (H + rps - 1) / rps : 0);
     } else {
       int4 rng = make_int4(0, 0, 0, 0);
@@ -351,17 +389,15 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
 
     // ---- phase A: G_ab of each converged spot into gtab[k][j]
     for (int j = 0; j < ns; ++j) {
-      {  // prefetch spot j + kAhead (this group's record, else the next group's range)
+      if (lane == 0) {  // prefetch spot j + kAhead (this group's record, else the next group's)
         const int t = j + kAhead;
         if (t < ns) {
           const int4 o = *reinterpret_cast<const int4 *>(&rec[t].off_lo);
           const int64_t ot = (int64_t)(((uint64_t)(uint32_t)o.y << 32) | (uint32_t)o.x);
-          if ((valid_mask >> t) & 1u)
-            prefetch_range(img, ot, (o.z & 0xff) * ((o.z >> 8) & 0xff), lane);
+          if ((valid_mask >> t) & 1u) prefetch_range(img, ot, (o.z & 0xff) * ((o.z >> 8) & 0xff));
         } else if (t - kGroup >= 0 && t - kGroup < kGroup) {
           const int4 r4 = nxt[t - kGroup];
-          prefetch_range(img, (int64_t)(((uint64_t)(uint32_t)r4.y << 32) | (uint32_t)r4.x), r4.z,
-                         lane);
+          prefetch_range(img, (int64_t)(((uint64_t)(uint32_t)r4.y << 32) | (uint32_t)r4.x), r4.z);
         }
       }
       if (!((conv_mask >> j) & 1u)) continue;
@@ -369,7 +405,9 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
       const float4 rb = *reinterpret_cast<const float4 *>(&rec[j].sh);
       const int4 rc = *reinterpret_cast<const int4 *>(&rec[j].off_lo);
       const float x0j = ra.x, y0j = ra.y, ivxj = ra.z, ivyj = ra.w, shj = rb.x, rWj = rb.y;
-      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = rc.z >> 16, nrj = rc.w;
+      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = (rc.z >> 16) & 0xff;
+      const bool fullj = rc.z >> 24;
+      const int nrj = rc.w;
       const T *const pj = img + (int64_t)(((uint64_t)(uint32_t)rc.y << 32) | (uint32_t)rc.x);
       // row table: e_y dy^b, b = 0..4 (zero beyond the ROI)
       {
@@ -383,33 +421,29 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
       const int yo = (int)(((float)lane + 0.5f) * rWj);
       const int xl = lane - yo * Wj;
       const bool plane = yo < rpsj;
-      float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f;
-      for (int t0 = 0; t0 < nrj; t0 += kChunk) {
-        float gv[kChunk];
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-          const int y = yo + (t0 + u) * rpsj;
-          gv[u] = plane && y < Hj ? ldpix(pj + (y * Wj + xl)) - shj : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-          const int y = min(yo + (t0 + u) * rpsj, 31);
-          const float4 r4 = *reinterpret_cast<const float4 *>(rowt + y * 8);
-          const float r5 = rowt[y * 8 + 4];
-          c0 = fmaf(gv[u], r4.x, c0);
-          c1 = fmaf(gv[u], r4.y, c1);
-          c2 = fmaf(gv[u], r4.z, c2);
-          c3 = fmaf(gv[u], r4.w, c3);
-          c4 = fmaf(gv[u], r5, c4);
-        }
+      float c[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      {
+        // this lane's rows yo, yo + rps, ...: nv of them
+        const int nv = plane ? (Hj - yo + rpsj - 1) / rpsj : 0;
+        const int step = rpsj * Wj, rs = rpsj * 8;
+        const T *p = pj + (yo * Wj + xl);
+        const float *rt = rowt + yo * 8;
+        int t0 = 0;
+        if (fullj)
+          for (; t0 + kChunk <= nrj; t0 += kChunk)
+            rows_a<T, false>(p + t0 * 32, 32, rt + t0 * rs, rs, 0, shj, c);
+        for (; t0 < nrj; t0 += kChunk)
+          rows_a<T, true>(p + t0 * step, step, rt + t0 * rs, rs, nv - t0, shj, c);
       }
+      // column x collects the partial sums of lanes x + t W, t < rps (the lanes' own values)
+      float c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
       for (int t = 1; t < rpsj; ++t) {
         const int d = t * Wj;
-        c0 += __shfl_down_sync(0xffffffffu, c0, d);
-        c1 += __shfl_down_sync(0xffffffffu, c1, d);
-        c2 += __shfl_down_sync(0xffffffffu, c2, d);
-        c3 += __shfl_down_sync(0xffffffffu, c3, d);
-        c4 += __shfl_down_sync(0xffffffffu, c4, d);
+        c0 += __shfl_down_sync(0xffffffffu, c[0], d);
+        c1 += __shfl_down_sync(0xffffffffu, c[1], d);
+        c2 += __shfl_down_sync(0xffffffffu, c[2], d);
+        c3 += __shfl_down_sync(0xffffffffu, c[3], d);
+        c4 += __shfl_down_sync(0xffffffffu, c[4], d);
       }
       {
         const float dx = (float)lane - x0j;
@@ -516,7 +550,9 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
       if (!((valid_mask >> j) & 1u)) continue;
       const int4 rc = *reinterpret_cast<const int4 *>(&rec[j].off_lo);
       const float4 rb = *reinterpret_cast<const float4 *>(&rec[j].sh);
-      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = rc.z >> 16, nrj = rc.w;
+      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = (rc.z >> 16) & 0xff;
+      const bool fullj = rc.z >> 24;
+      const int nrj = rc.w;
       const int64_t offj = (int64_t)(((uint64_t)(uint32_t)rc.y << 32) | (uint32_t)rc.x);
       const T *const pj = img + offj;
       float *const gj = a.grad + offj;
@@ -531,34 +567,34 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BwdArgs a) {
       const float4 ra = *reinterpret_cast<const float4 *>(&rec[j].x0);
       const float4 rv = *reinterpret_cast<const float4 *>(&rec[j].vx);
       const float4 rw = *reinterpret_cast<const float4 *>(&rec[j].va);
-      const float shj = rb.x, alj = rb.z, bpj = rb.w;
+      const float alj = rb.z, betaj = rb.x + rb.w;
       const float vaj = rw.x, vbj = rw.y, ccj = rw.z;
+      // grad = f (alpha (A(x) + B(y)) + va) + vb + cchi (g - alpha f - beta)
+      //      = e_x e_y (K1 + alpha B(y)) + cchi g + K2
       {
         const float dy = (float)lane - ra.y;
         const float e = lane < Hj ? __expf(-0.5f * dy * dy * ra.w) : 0.f;
-        rowb[lane] = make_float2(e, dy * fmaf(rv.w, dy, rv.y));
+        rowb[lane] = make_float2(e, alj * dy * fmaf(rv.w, dy, rv.y));
       }
       __syncwarp();
       const float dx = (float)xl - ra.x;
       const float ex = __expf(-0.5f * dx * dx * ra.z);
-      const float Ax = dx * fmaf(rv.z, dx, rv.x);
-      for (int t0 = 0; t0 < nrj; t0 += kChunk) {
-        float gv[kChunk];
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-          const int y = yo + (t0 + u) * rpsj;
-          gv[u] = plane && y < Hj ? ldpix(pj + (y * Wj + xl)) - shj : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-          const int y = yo + (t0 + u) * rpsj;
-          if (plane && y < Hj) {
-            const float2 eb = rowb[y];
-            const float f = ex * eb.x;
-            const float r = gv[u] - fmaf(alj, f, bpj);
-            gj[y * Wj + xl] = fmaf(f, fmaf(alj, Ax + eb.y, vaj), vbj) + ccj * r;
-          }
-        }
+      const float K1 = fmaf(alj, dx * fmaf(rv.z, dx, rv.x), vaj) - ccj * alj;
+      const float K2 = fmaf(-ccj, betaj, vbj);
+      {
+        const int nv = plane ? (Hj - yo + rpsj - 1) / rpsj : 0;
+        const int step = rpsj * Wj;
+        const T *p = pj + (yo * Wj + xl);
+        float *q = gj + (yo * Wj + xl);
+        const float2 *rt = rowb + yo;
+        int t0 = 0;
+        if (fullj)
+          for (; t0 + kChunk <= nrj; t0 += kChunk)
+            rows_b<T, false>(p + t0 * 32, q + t0 * 32, 32, rt + t0 * rpsj, rpsj, 0, ex, K1, ccj,
+                             K2);
+        for (; t0 < nrj; t0 += kChunk)
+          rows_b<T, true>(p + t0 * step, q + t0 * step, step, rt + t0 * rpsj, rpsj, nv - t0, ex,
+                          K1, ccj, K2);
       }
       __syncwarp();
     }

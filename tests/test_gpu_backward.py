@@ -58,6 +58,64 @@ def test_backward_matches_oracle_ift_on_iso16():
     assert np.median(errs) <= 1e-5
 
 
+def _oracle_errors(b, out, up):
+    """Per-spot relative error of the GPU pixel gradient against the oracle's FP64 backward
+    at the oracle's own tight fit; also the determined mask of those fits."""
+    import oracle
+    from tests.parity import determined
+    gp, ga, gb, gc = up
+    grad = fitspots.backward(b.images.to(DEV), b.offsets.to(DEV), b.dims.to(DEV),
+                             b.model.to(DEV), out, gp, ga, gb, gc)
+    torch.cuda.synchronize()
+    grad = grad.cpu().numpy()
+    d = b.numpy()
+    img = synth.as_numpy_images(b)
+    ref = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"], max_iter=300,
+                           min_delta=0.0, min_step=1e-13)
+    det = determined(b, ref)
+    errs = np.full(b.n, np.inf)
+    for s in np.nonzero(det)[0]:
+        off = int(d["offsets"][s])
+        W, H = int(d["dims"][s, 0]), int(d["dims"][s, 1])
+        gs = img[off:off + W * H].astype(np.float64)
+        u = np.concatenate([gp[s].numpy(), [ga[s], gb[s], gc[s]]]).astype(np.float64)
+        ro = oracle.backward(int(d["model"][s]), W, H, gs, ref["params"][s], ref["alpha"][s],
+                             ref["beta"][s], u)
+        if ro is not None:
+            errs[s] = np.linalg.norm(grad[off:off + W * H] - ro) / np.linalg.norm(ro)
+    return errs, det
+
+
+def test_backward_matches_oracle_mixed_sizes():
+    """Sizes 5..32 per side (row steps that do and do not divide the warp, odd heights,
+    partial row groups) and both models: same per-spot bar as the 16x16 workload on the
+    determined spots."""
+    n = 1500
+    b = synth.make_workload("mixed", n)
+    out = fitspots.fit_batch(b.to(DEV), **TIGHT)
+    errs, det = _oracle_errors(b, out, _upstream(n, 5))
+    e = errs[det]
+    print(f"mixed backward: {det.sum()} determined of {n}; median rel err {np.median(e):.2e}, "
+          f"p99.9 {np.percentile(e, 99.9):.2e}, max {e.max():.2e}")
+    assert det.sum() >= n // 3
+    assert np.mean(e <= 1e-4) >= 0.999
+    assert np.median(e) <= 1e-5
+
+
+def test_backward_matches_oracle_uint16_ell32():
+    """uint16 pixels, elliptic model, 32x32 (one row per step)."""
+    n = 400
+    b = synth.make_workload("ell32", n)
+    out = fitspots.fit_batch(b.to(DEV), **TIGHT)
+    errs, det = _oracle_errors(b, out, _upstream(n, 6))
+    e = errs[det]
+    print(f"ell32 backward: {det.sum()} determined of {n}; median rel err {np.median(e):.2e}, "
+          f"p99.9 {np.percentile(e, 99.9):.2e}, max {e.max():.2e}")
+    assert det.sum() >= 50
+    assert np.mean(e <= 1e-4) >= 0.999
+    assert np.median(e) <= 1e-5
+
+
 def test_backward_identities_both_models():
     """Shift and scale invariance of the fit fix sum_i dq/dg_i and sum_i g_i dq/dg_i."""
     for name in ("iso16", "ell32"):

@@ -62,9 +62,31 @@ struct BwdArgs {
   float *grad;
 };
 
-template <typename T>
-__device__ __forceinline__ float ldpix(const T *p) {
-  return (float)__ldg(p);
+// L2 policies: a group's pixels are read in phase A and again in phase B; phase A and the
+// prefetch mark them evict-last, phase B's second read and the gradient stores evict-first,
+// so that the write stream does not push out pixels still waiting for phase B.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float ldpix(const float *p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ldpix(const unsigned short *p, uint64_t pol) {
+  unsigned short v;
+  asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return (float)v;
+}
+__device__ __forceinline__ void stgrad(float *q, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(q), "f"(v), "l"(pol) : "memory");
 }
 
 // bilinear data sums G_ab (slot: (a, b))
@@ -117,11 +139,12 @@ __device__ __forceinline__ void back_step(const float (&M)[6][6], float (&v)[6])
 // Prefetch into L2 the pixel range [off, off + npx) of a spot with one bulk prefetch, the
 // range widened to 16-byte boundaries (which stay inside the pages the range touches).
 template <typename T>
-__device__ __forceinline__ void prefetch_range(const T *img, int64_t off, int npx) {
+__device__ __forceinline__ void prefetch_range(const T *img, int64_t off, int npx, uint64_t pol) {
   if (npx <= 0) return;
   const uintptr_t lo = reinterpret_cast<uintptr_t>(img + off) & ~uintptr_t(15);
   const uintptr_t hi = (reinterpret_cast<uintptr_t>(img + off + npx) + 15) & ~uintptr_t(15);
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo))
+  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(lo),
+               "r"((uint32_t)(hi - lo)), "l"(pol)
                : "memory");
 }
 
@@ -130,10 +153,11 @@ __device__ __forceinline__ void prefetch_range(const T *img, int64_t off, int np
 // `nleft` rows count.
 template <typename T, bool kPred>
 __device__ __forceinline__ void rows_a(const T *p, int step, const float *rt, int rs, int nleft,
-                                       float sh, float (&c)[5]) {
+                                       float sh, uint64_t pol, float (&c)[5]) {
   float gv[kChunk];
 #pragma unroll
-  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * step) - sh : 0.f;
+  for (int u = 0; u < kChunk; ++u)
+    gv[u] = !kPred || u < nleft ? ldpix(p + u * step, pol) - sh : 0.f;
 #pragma unroll
   for (int u = 0; u < kChunk; ++u) {
     const float *r = rt + (kPred ? min(u, max(nleft - 1, 0)) : u) * rs;
@@ -151,15 +175,16 @@ __device__ __forceinline__ void rows_a(const T *p, int step, const float *rt, in
 // table rb = (e_y, alpha B(y)); same row addressing as rows_a.
 template <typename T, bool kPred>
 __device__ __forceinline__ void rows_b(const T *p, float *q, int step, const float2 *rb, int rs,
-                                       int nleft, float ex, float K1, float cc, float K2) {
+                                       int nleft, float ex, float K1, float cc, float K2,
+                                       uint64_t pol) {
   float gv[kChunk];
 #pragma unroll
-  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * step) : 0.f;
+  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * step, pol) : 0.f;
 #pragma unroll
   for (int u = 0; u < kChunk; ++u)
     if (!kPred || u < nleft) {
       const float2 eb = rb[u * rs];
-      q[u * step] = fmaf(ex * eb.x, K1 + eb.y, fmaf(cc, gv[u], K2));
+      stgrad(q + u * step, fmaf(ex * eb.x, K1 + eb.y, fmaf(cc, gv[u], K2)), pol);
     }
 }
 
@@ -310,6 +335,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
   __shared__ float4 sm4[kBwdWarps * kBwdWarpFloats / 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T *const img = static_cast<const T *>(a.images);
+  const uint64_t keep = policy_evict_last(), drop = policy_evict_first();
   float *const rowt = reinterpret_cast<float *>(sm4) + warp * kBwdWarpFloats;  // [32][8]
   float *const red = rowt + 32 * 8;                                            // [kNG][36]
   float *const gtab = red + kNG * kRedStride;                                  // [kNG][17]
@@ -327,7 +353,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
     const int64_t off = a.offsets[s];
     if (W >= 1 && H >= 1 && W <= 32 && H <= 32 && off >= 0 &&
         off + (int64_t)W * H <= a.image_elems)
-      prefetch_range(img, off, W * H);
+      prefetch_range(img, off, W * H, keep);
   }
   for (; g < ngroups; g += gstride) {
     const int s0 = g * kGroup;
@@ -394,10 +420,12 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
         if (t < ns) {
           const int4 o = *reinterpret_cast<const int4 *>(&rec[t].off_lo);
           const int64_t ot = (int64_t)(((uint64_t)(uint32_t)o.y << 32) | (uint32_t)o.x);
-          if ((valid_mask >> t) & 1u) prefetch_range(img, ot, (o.z & 0xff) * ((o.z >> 8) & 0xff));
+          if ((valid_mask >> t) & 1u)
+            prefetch_range(img, ot, (o.z & 0xff) * ((o.z >> 8) & 0xff), keep);
         } else if (t - kGroup >= 0 && t - kGroup < kGroup) {
           const int4 r4 = nxt[t - kGroup];
-          prefetch_range(img, (int64_t)(((uint64_t)(uint32_t)r4.y << 32) | (uint32_t)r4.x), r4.z);
+          prefetch_range(img, (int64_t)(((uint64_t)(uint32_t)r4.y << 32) | (uint32_t)r4.x), r4.z,
+                         keep);
         }
       }
       if (!((conv_mask >> j) & 1u)) continue;
@@ -431,9 +459,9 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
         int t0 = 0;
         if (fullj)
           for (; t0 + kChunk <= nrj; t0 += kChunk)
-            rows_a<T, false>(p + t0 * 32, 32, rt + t0 * rs, rs, 0, shj, c);
+            rows_a<T, false>(p + t0 * 32, 32, rt + t0 * rs, rs, 0, shj, keep, c);
         for (; t0 < nrj; t0 += kChunk)
-          rows_a<T, true>(p + t0 * step, step, rt + t0 * rs, rs, nv - t0, shj, c);
+          rows_a<T, true>(p + t0 * step, step, rt + t0 * rs, rs, nv - t0, shj, keep, c);
       }
       // column x collects the partial sums of lanes x + t W, t < rps (the lanes' own values)
       float c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
@@ -561,7 +589,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
       const bool plane = yo < rpsj;
       if (!((ok_mask >> j) & 1u)) {  // no gradient through fits that did not converge
         if (plane)
-          for (int y = yo; y < Hj; y += rpsj) gj[y * Wj + xl] = 0.f;
+          for (int y = yo; y < Hj; y += rpsj) stgrad(gj + (y * Wj + xl), 0.f, drop);
         continue;
       }
       const float4 ra = *reinterpret_cast<const float4 *>(&rec[j].x0);
@@ -591,10 +619,10 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
         if (fullj)
           for (; t0 + kChunk <= nrj; t0 += kChunk)
             rows_b<T, false>(p + t0 * 32, q + t0 * 32, 32, rt + t0 * rpsj, rpsj, 0, ex, K1, ccj,
-                             K2);
+                             K2, drop);
         for (; t0 < nrj; t0 += kChunk)
           rows_b<T, true>(p + t0 * step, q + t0 * step, step, rt + t0 * rpsj, rpsj, nv - t0, ex,
-                          K1, ccj, K2);
+                          K1, ccj, K2, drop);
       }
       __syncwarp();
     }

@@ -39,14 +39,21 @@ constexpr int kGroup = 16;   // spots per warp group: lane j and lane j + 16 ser
 constexpr int kAhead = 3;    // spots prefetched into L2 ahead of phase A
 constexpr int kNG = 13;      // bilinear data sums G_ab
 constexpr int kGStride = kGroup + 1;
-constexpr int kRedStride = 36;  // reduction row stride (floats): float4 rows on distinct banks
 constexpr int kChunk = 8;    // pixel rows a lane loads before it computes on them
 constexpr int kRec = 20;     // per-spot record (floats)
-// per warp: row table [32][8], reduction rows [kNG][kRedStride], group table [kNG][kGStride],
-// spot records [kGroup][kRec], next-group pixel ranges [kGroup] int4, pass-B row table [32] float2
+// Pixel passes take one spot per warp (32 lanes) or, when two consecutive spots are both at
+// most 16 wide, one spot per half-warp. Reduction rows: [13][36] for one spot, [2][13][20]
+// for a pair (stride chosen so a quarter-warp's float4 rows fall on distinct banks).
+constexpr int kRedStride1 = 36, kRedStride2 = 20;
+constexpr int kRedFloats = 2 * kNG * kRedStride2 > kNG * kRedStride1 ? 2 * kNG * kRedStride2
+                                                                     : kNG * kRedStride1;
+// per warp: phase A row tables [64] float4 + [64] float and the reduction rows, which phase B
+// reuses for its row table [64] float2; group table [kNG][kGStride]; spot records
+// [kGroup][kRec]; next-group pixel ranges [kGroup] int4
+constexpr int kPassFloats = 64 * 4 + 64 + kRedFloats;
 constexpr int kGTabFloats = (kNG * kGStride + 3) / 4 * 4;
-constexpr int kBwdWarpFloats =
-    32 * 8 + kNG * kRedStride + kGTabFloats + kGroup * kRec + kGroup * 4 + 32 * 2;
+constexpr int kBwdWarpFloats = kPassFloats + kGTabFloats + kGroup * kRec + kGroup * 4;
+static_assert(kPassFloats >= 64 * 2, "phase B row table");
 
 struct BwdArgs {
   const void *images;
@@ -149,20 +156,22 @@ __device__ __forceinline__ void prefetch_range(const T *img, int64_t off, int np
 }
 
 // Phase A rows of one lane: c_b += g' e_y dy^b over kChunk rows starting at p (pixels) and
-// rt (row table), rows `step` pixels and `rs` table floats apart; with kPred only the first
-// `nleft` rows count.
-template <typename T, bool kPred>
-__device__ __forceinline__ void rows_a(const T *p, int step, const float *rt, int rs, int nleft,
-                                       float sh, uint64_t pol, float (&c)[5]) {
+// row r0 of the row tables, rows `step` pixels (kStep if nonzero) and `rs` table rows apart;
+// with kPred only the first `nleft` rows count.
+template <typename T, bool kPred, int kStep>
+__device__ __forceinline__ void rows_a(const T *p, int step, const float4 *t4, const float *t1,
+                                       int rs, int nleft, float sh, uint64_t pol,
+                                       float (&c)[5]) {
+  const int st = kStep ? kStep : step;
   float gv[kChunk];
 #pragma unroll
   for (int u = 0; u < kChunk; ++u)
-    gv[u] = !kPred || u < nleft ? ldpix(p + u * step, pol) - sh : 0.f;
+    gv[u] = !kPred || u < nleft ? ldpix(p + u * st, pol) - sh : 0.f;
 #pragma unroll
   for (int u = 0; u < kChunk; ++u) {
-    const float *r = rt + (kPred ? min(u, max(nleft - 1, 0)) : u) * rs;
-    const float4 r4 = *reinterpret_cast<const float4 *>(r);
-    const float r5 = r[4];
+    const int r = (kPred ? min(u, max(nleft - 1, 0)) : u) * rs;
+    const float4 r4 = t4[r];
+    const float r5 = t1[r];
     c[0] = fmaf(gv[u], r4.x, c[0]);
     c[1] = fmaf(gv[u], r4.y, c[1]);
     c[2] = fmaf(gv[u], r4.z, c[2]);
@@ -173,20 +182,29 @@ __device__ __forceinline__ void rows_a(const T *p, int step, const float *rt, in
 
 // Phase B rows of one lane: grad = e_x e_y (K1 + alpha B(y)) + u_chi g + K2 with the row
 // table rb = (e_y, alpha B(y)); same row addressing as rows_a.
-template <typename T, bool kPred>
+template <typename T, bool kPred, int kStep>
 __device__ __forceinline__ void rows_b(const T *p, float *q, int step, const float2 *rb, int rs,
                                        int nleft, float ex, float K1, float cc, float K2,
                                        uint64_t pol) {
+  const int st = kStep ? kStep : step;
   float gv[kChunk];
 #pragma unroll
-  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * step, pol) : 0.f;
+  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * st, pol) : 0.f;
 #pragma unroll
   for (int u = 0; u < kChunk; ++u)
     if (!kPred || u < nleft) {
       const float2 eb = rb[u * rs];
-      stgrad(q + u * step, fmaf(ex * eb.x, K1 + eb.y, fmaf(cc, gv[u], K2)), pol);
+      stgrad(q + u * st, fmaf(ex * eb.x, K1 + eb.y, fmaf(cc, gv[u], K2)), pol);
     }
 }
+
+// The rows of one lane in a pixel pass: a warp-uniform fast path when every lane has the same
+// number of rows a full row step apart (step = lanes per spot), else per-lane predication.
+struct LaneRows {
+  int nv;      // this lane's rows
+  int nmax;    // most rows of any lane of the warp
+  bool fast;   // every lane: nv == nmax, step == lanes per spot
+};
 
 // The spot's record: geometry and profile (phase A), solution coefficients (phase B).
 struct SpotRec {
@@ -194,7 +212,9 @@ struct SpotRec {
   float sh, rW, al, bp;
   float vx, vy, vsx, vsy;   // v . K coefficients of the 1-D parts (already times 1/s^2, 1/s^3)
   float va, vb, cchi, pad;
-  int off_lo, off_hi, whr, nrow;  // whr = W | H << 8 | rows-per-step << 16 | full << 24
+  int off_lo, off_hi;
+  int whr;   // W | H << 8 | (32 / W) << 16 | (16 / W) << 24: rows per step for 32 and 16 lanes
+  int nrow;  // row steps for 32 lanes | for 16 lanes << 8 | full for 32 << 16 | full for 16 << 17
 };
 static_assert(sizeof(SpotRec) == kRec * 4, "record size");
 
@@ -336,12 +356,14 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T *const img = static_cast<const T *>(a.images);
   const uint64_t keep = policy_evict_last(), drop = policy_evict_first();
-  float *const rowt = reinterpret_cast<float *>(sm4) + warp * kBwdWarpFloats;  // [32][8]
-  float *const red = rowt + 32 * 8;                                            // [kNG][36]
-  float *const gtab = red + kNG * kRedStride;                                  // [kNG][17]
-  SpotRec *const rec = reinterpret_cast<SpotRec *>(gtab + kGTabFloats);        // [kGroup]
+  float *const wbase = reinterpret_cast<float *>(sm4) + warp * kBwdWarpFloats;
+  float4 *const rowt4 = reinterpret_cast<float4 *>(wbase);                // [2][32]: e_y dy^0..3
+  float *const rowt1 = wbase + 64 * 4;                                     // [2][32]: e_y dy^4
+  float *const red = rowt1 + 64;                                           // reduction rows
+  float2 *const rowb = reinterpret_cast<float2 *>(wbase);                  // phase B [2][32]
+  float *const gtab = wbase + kPassFloats;                                 // [kNG][17]
+  SpotRec *const rec = reinterpret_cast<SpotRec *>(gtab + kGTabFloats);    // [kGroup]
   int4 *const nxt = reinterpret_cast<int4 *>(rec + kGroup);  // next group: offset, pixels
-  float2 *const rowb = reinterpret_cast<float2 *>(nxt + kGroup);               // [32]
   const int ngroups = (a.n + kGroup - 1) / kGroup;
   const int gstride = gridDim.x * kBwdWarps;
   const int jl = lane & (kGroup - 1);  // the group spot this lane serves in phases 0 and S
@@ -384,17 +406,21 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
     }
     const float ivx = 1.f / (sx * sx), ivy = 1.f / (sy * sy);
     const float sh = rintf(be), bp = be - sh;
-    const int rps = valid ? 32 / W : 1;
-    // every lane has the same rows: a row step covers 32 pixels and H is a multiple of it
+    // rows per step for 32 and for 16 lanes per spot; a layout is full when a row step covers
+    // all its lanes and H is a multiple of it (every lane then has the same rows)
+    const int rps = valid ? 32 / W : 1, rps2 = valid ? max(16 / W, 1) : 1;
     const bool full = valid && rps * W == 32 && H % rps == 0;
+    const bool full2 = valid && W <= 16 && rps2 * W == 16 && H % rps2 == 0;
     if (!ylane) {
       SpotRec &r = rec[jl];
       *reinterpret_cast<float4 *>(&r.x0) = make_float4(x0, y0, ivx, ivy);
       *reinterpret_cast<float4 *>(&r.sh) = make_float4(sh, valid ? 1.f / (float)W : 1.f, al, bp);
       *reinterpret_cast<int4 *>(&r.off_lo) =
           make_int4((int)(off & 0xffffffff), (int)(off >> 32),
-                    W | (H << 8) | (rps << 16) | ((int)full << 24),
-                    valid ? (H + rps - 1) / rps : 0);
+                    W | (H << 8) | (rps << 16) | (rps2 << 24),
+                    valid ? ((H + rps - 1) / rps) | (((H + rps2 - 1) / rps2) << 8) |
+                                ((int)full << 16) | ((int)full2 << 17)
+                          : 0);
     } else {
       int4 rng = make_int4(0, 0, 0, 0);
       if (g + gstride < ngroups) {
@@ -414,9 +440,9 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
     __syncwarp();
 
     // ---- phase A: G_ab of each converged spot into gtab[k][j]
-    for (int j = 0; j < ns; ++j) {
-      if (lane == 0) {  // prefetch spot j + kAhead (this group's record, else the next group's)
-        const int t = j + kAhead;
+    for (int j = 0; j < ns;) {
+      if (lane < 2) {  // prefetch spot j + kAhead + lane (this group's, else the next group's)
+        const int t = j + kAhead + lane;
         if (t < ns) {
           const int4 o = *reinterpret_cast<const int4 *>(&rec[t].off_lo);
           const int64_t ot = (int64_t)(((uint64_t)(uint32_t)o.y << 32) | (uint32_t)o.x);
@@ -428,87 +454,122 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
                          keep);
         }
       }
-      if (!((conv_mask >> j) & 1u)) continue;
-      const float4 ra = *reinterpret_cast<const float4 *>(&rec[j].x0);
-      const float4 rb = *reinterpret_cast<const float4 *>(&rec[j].sh);
-      const int4 rc = *reinterpret_cast<const int4 *>(&rec[j].off_lo);
+      if (!((conv_mask >> j) & 1u)) {
+        ++j;
+        continue;
+      }
+      const bool pair = j + 1 < ns && ((conv_mask >> (j + 1)) & 1u) &&
+                        (rec[j].whr & 0xff) <= 16 && (rec[j + 1].whr & 0xff) <= 16;
+      const int L = pair ? 16 : 32;
+      const int h = pair ? lane >> 4 : 0;  // which spot of the step this lane serves
+      const int ln = lane & (L - 1);       // lane within the spot
+      const int js = j + h;
+      const float4 ra = *reinterpret_cast<const float4 *>(&rec[js].x0);
+      const float4 rb = *reinterpret_cast<const float4 *>(&rec[js].sh);
+      const int4 rc = *reinterpret_cast<const int4 *>(&rec[js].off_lo);
       const float x0j = ra.x, y0j = ra.y, ivxj = ra.z, ivyj = ra.w, shj = rb.x, rWj = rb.y;
-      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = (rc.z >> 16) & 0xff;
-      const bool fullj = rc.z >> 24;
-      const int nrj = rc.w;
+      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff;
+      const int rpsj = pair ? rc.z >> 24 : (rc.z >> 16) & 0xff;
+      const int nrj = pair ? (rc.w >> 8) & 0xff : rc.w & 0xff;
+      const bool fullj = (rc.w >> (pair ? 17 : 16)) & 1;
       const T *const pj = img + (int64_t)(((uint64_t)(uint32_t)rc.y << 32) | (uint32_t)rc.x);
+      float4 *const t4 = rowt4 + h * 32;
+      float *const t1 = rowt1 + h * 32;
       // row table: e_y dy^b, b = 0..4 (zero beyond the ROI)
-      {
-        const float dy = (float)lane - y0j;
-        const float e = lane < Hj ? __expf(-0.5f * dy * dy * ivyj) : 0.f;
+      for (int r = ln; r < 32; r += L) {
+        const float dy = (float)r - y0j;
+        const float e = r < Hj ? __expf(-0.5f * dy * dy * ivyj) : 0.f;
         const float e1 = e * dy, e2 = e1 * dy, e3 = e2 * dy;
-        *reinterpret_cast<float4 *>(rowt + lane * 8) = make_float4(e, e1, e2, e3);
-        rowt[lane * 8 + 4] = e3 * dy;
+        t4[r] = make_float4(e, e1, e2, e3);
+        t1[r] = e3 * dy;
       }
       __syncwarp();
-      const int yo = (int)(((float)lane + 0.5f) * rWj);
-      const int xl = lane - yo * Wj;
+      const int yo = (int)(((float)ln + 0.5f) * rWj);
+      const int xl = ln - yo * Wj;
       const bool plane = yo < rpsj;
+      // this lane's rows yo, yo + rps, ...: nv of them
+      const int nv = plane && yo < Hj ? (int)(((float)(Hj - yo - 1) + 0.5f) / (float)rpsj) + 1 : 0;
+      const int nmax = pair ? max(nrj, __shfl_xor_sync(0xffffffffu, nrj, 16)) : nrj;
+      const bool fast = __all_sync(0xffffffffu, fullj && nrj == nmax);
       float c[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       {
-        // this lane's rows yo, yo + rps, ...: nv of them
-        const int nv = plane ? (Hj - yo + rpsj - 1) / rpsj : 0;
-        const int step = rpsj * Wj, rs = rpsj * 8;
+        const int step = rpsj * Wj;
         const T *p = pj + (yo * Wj + xl);
-        const float *rt = rowt + yo * 8;
+        const float4 *r4 = t4 + yo;
+        const float *r1 = t1 + yo;
         int t0 = 0;
-        if (fullj)
-          for (; t0 + kChunk <= nrj; t0 += kChunk)
-            rows_a<T, false>(p + t0 * 32, 32, rt + t0 * rs, rs, 0, shj, keep, c);
-        for (; t0 < nrj; t0 += kChunk)
-          rows_a<T, true>(p + t0 * step, step, rt + t0 * rs, rs, nv - t0, shj, keep, c);
+        if (fast) {
+          if (pair)
+            for (; t0 + kChunk <= nmax; t0 += kChunk)
+              rows_a<T, false, 16>(p + t0 * 16, 16, r4 + t0 * rpsj, r1 + t0 * rpsj, rpsj, 0, shj,
+                                   keep, c);
+          else
+            for (; t0 + kChunk <= nmax; t0 += kChunk)
+              rows_a<T, false, 32>(p + t0 * 32, 32, r4 + t0 * rpsj, r1 + t0 * rpsj, rpsj, 0, shj,
+                                   keep, c);
+        }
+        for (; t0 < nmax; t0 += kChunk)
+          rows_a<T, true, 0>(p + t0 * step, step, r4 + t0 * rpsj, r1 + t0 * rpsj, rpsj, nv - t0,
+                             shj, keep, c);
       }
-      // column x collects the partial sums of lanes x + t W, t < rps (the lanes' own values)
+      // column x collects the partial sums of lanes x + t W, t < rps, of its own spot
       float c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
-      for (int t = 1; t < rpsj; ++t) {
-        const int d = t * Wj;
-        c0 += __shfl_down_sync(0xffffffffu, c[0], d);
-        c1 += __shfl_down_sync(0xffffffffu, c[1], d);
-        c2 += __shfl_down_sync(0xffffffffu, c[2], d);
-        c3 += __shfl_down_sync(0xffffffffu, c[3], d);
-        c4 += __shfl_down_sync(0xffffffffu, c[4], d);
+      const int rmax = pair ? max(rpsj, __shfl_xor_sync(0xffffffffu, rpsj, 16)) : rpsj;
+      for (int t = 1; t < rmax; ++t) {
+        const int d = t < rpsj ? t * Wj : 0;
+        const float z0 = __shfl_down_sync(0xffffffffu, c[0], d, L);
+        const float z1 = __shfl_down_sync(0xffffffffu, c[1], d, L);
+        const float z2 = __shfl_down_sync(0xffffffffu, c[2], d, L);
+        const float z3 = __shfl_down_sync(0xffffffffu, c[3], d, L);
+        const float z4 = __shfl_down_sync(0xffffffffu, c[4], d, L);
+        if (t < rpsj) {
+          c0 += z0;
+          c1 += z1;
+          c2 += z2;
+          c3 += z3;
+          c4 += z4;
+        }
       }
       {
-        const float dx = (float)lane - x0j;
-        const float p0 = lane < Wj ? __expf(-0.5f * dx * dx * ivxj) : 0.f;
+        const int RS = pair ? kRedStride2 : kRedStride1;
+        float *const rr = red + h * kNG * RS + ln;
+        const float dx = (float)ln - x0j;
+        const float p0 = ln < Wj ? __expf(-0.5f * dx * dx * ivxj) : 0.f;
         const float p1 = p0 * dx, p2 = p1 * dx, p3 = p2 * dx, p4 = p3 * dx;
-        red[G00 * kRedStride + lane] = p0 * c0;
-        red[G10 * kRedStride + lane] = p1 * c0;
-        red[G01 * kRedStride + lane] = p0 * c1;
-        red[G20 * kRedStride + lane] = p2 * c0;
-        red[G02 * kRedStride + lane] = p0 * c2;
-        red[G11 * kRedStride + lane] = p1 * c1;
-        red[G30 * kRedStride + lane] = p3 * c0;
-        red[G03 * kRedStride + lane] = p0 * c3;
-        red[G12 * kRedStride + lane] = p1 * c2;
-        red[G21 * kRedStride + lane] = p2 * c1;
-        red[G40 * kRedStride + lane] = p4 * c0;
-        red[G22 * kRedStride + lane] = p2 * c2;
-        red[G04 * kRedStride + lane] = p0 * c4;
+        rr[G00 * RS] = p0 * c0;
+        rr[G10 * RS] = p1 * c0;
+        rr[G01 * RS] = p0 * c1;
+        rr[G20 * RS] = p2 * c0;
+        rr[G02 * RS] = p0 * c2;
+        rr[G11 * RS] = p1 * c1;
+        rr[G30 * RS] = p3 * c0;
+        rr[G03 * RS] = p0 * c3;
+        rr[G12 * RS] = p1 * c2;
+        rr[G21 * RS] = p2 * c1;
+        rr[G40 * RS] = p4 * c0;
+        rr[G22 * RS] = p2 * c2;
+        rr[G04 * RS] = p0 * c4;
+        __syncwarp();
+        if (lane < (pair ? 2 * kNG : kNG)) {
+          const int hh = lane >= kNG, k = lane - hh * kNG;
+          const float4 *r = reinterpret_cast<const float4 *>(red + (hh * kNG + k) * RS);
+          const int nq = ((rec[j + hh].whr & 0xff) + 3) >> 2;
+          float q0 = 0.f, q1 = 0.f;
+          int i = 0;
+          for (; i + 1 < nq; i += 2) {
+            const float4 w0 = r[i], w1 = r[i + 1];
+            q0 += (w0.x + w0.y) + (w0.z + w0.w);
+            q1 += (w1.x + w1.y) + (w1.z + w1.w);
+          }
+          if (i < nq) {
+            const float4 w0 = r[i];
+            q0 += (w0.x + w0.y) + (w0.z + w0.w);
+          }
+          gtab[k * kGStride + j + hh] = q0 + q1;
+        }
       }
       __syncwarp();
-      if (lane < kNG) {
-        const float4 *r = reinterpret_cast<const float4 *>(red + lane * kRedStride);
-        const int nq = (Wj + 3) >> 2;
-        float q0 = 0.f, q1 = 0.f;
-        int i = 0;
-        for (; i + 1 < nq; i += 2) {
-          const float4 w0 = r[i], w1 = r[i + 1];
-          q0 += (w0.x + w0.y) + (w0.z + w0.w);
-          q1 += (w1.x + w1.y) + (w1.z + w1.w);
-        }
-        if (i < nq) {
-          const float4 w0 = r[i];
-          q0 += (w0.x + w0.y) + (w0.z + w0.w);
-        }
-        gtab[lane * kGStride + j] = q0 + q1;
-      }
-      __syncwarp();
+      j += pair ? 2 : 1;
     }
 
     // ---- phase S: lane j (x moments, the solve) and lane j + 16 (y moments) for spot j
@@ -574,57 +635,80 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
     __syncwarp();
 
     // ---- phase B: grad_g = e_x e_y (alpha (A(x) + B(y)) + va) + vb + cchi (g' - alpha f - bp)
-    for (int j = 0; j < ns; ++j) {
-      if (!((valid_mask >> j) & 1u)) continue;
-      const int4 rc = *reinterpret_cast<const int4 *>(&rec[j].off_lo);
-      const float4 rb = *reinterpret_cast<const float4 *>(&rec[j].sh);
-      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff, rpsj = (rc.z >> 16) & 0xff;
-      const bool fullj = rc.z >> 24;
-      const int nrj = rc.w;
+    for (int j = 0; j < ns;) {
+      if (!((valid_mask >> j) & 1u)) {
+        ++j;
+        continue;
+      }
+      if (!((ok_mask >> j) & 1u)) {  // no gradient through fits that did not converge
+        const int4 rc = *reinterpret_cast<const int4 *>(&rec[j].off_lo);
+        const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff;
+        float *const gj = a.grad + (int64_t)(((uint64_t)(uint32_t)rc.y << 32) | (uint32_t)rc.x);
+        for (int i = lane; i < Wj * Hj; i += 32) stgrad(gj + i, 0.f, drop);
+        ++j;
+        continue;
+      }
+      const bool pair = j + 1 < ns && ((ok_mask >> (j + 1)) & 1u) &&
+                        (rec[j].whr & 0xff) <= 16 && (rec[j + 1].whr & 0xff) <= 16;
+      const int L = pair ? 16 : 32;
+      const int h = pair ? lane >> 4 : 0;
+      const int ln = lane & (L - 1);
+      const int js = j + h;
+      const int4 rc = *reinterpret_cast<const int4 *>(&rec[js].off_lo);
+      const float4 rb = *reinterpret_cast<const float4 *>(&rec[js].sh);
+      const float4 ra = *reinterpret_cast<const float4 *>(&rec[js].x0);
+      const float4 rv = *reinterpret_cast<const float4 *>(&rec[js].vx);
+      const float4 rw = *reinterpret_cast<const float4 *>(&rec[js].va);
+      const int Wj = rc.z & 0xff, Hj = (rc.z >> 8) & 0xff;
+      const int rpsj = pair ? rc.z >> 24 : (rc.z >> 16) & 0xff;
+      const int nrj = pair ? (rc.w >> 8) & 0xff : rc.w & 0xff;
+      const bool fullj = (rc.w >> (pair ? 17 : 16)) & 1;
       const int64_t offj = (int64_t)(((uint64_t)(uint32_t)rc.y << 32) | (uint32_t)rc.x);
       const T *const pj = img + offj;
       float *const gj = a.grad + offj;
-      const int yo = (int)(((float)lane + 0.5f) * rb.y);
-      const int xl = lane - yo * Wj;
-      const bool plane = yo < rpsj;
-      if (!((ok_mask >> j) & 1u)) {  // no gradient through fits that did not converge
-        if (plane)
-          for (int y = yo; y < Hj; y += rpsj) stgrad(gj + (y * Wj + xl), 0.f, drop);
-        continue;
-      }
-      const float4 ra = *reinterpret_cast<const float4 *>(&rec[j].x0);
-      const float4 rv = *reinterpret_cast<const float4 *>(&rec[j].vx);
-      const float4 rw = *reinterpret_cast<const float4 *>(&rec[j].va);
       const float alj = rb.z, betaj = rb.x + rb.w;
       const float vaj = rw.x, vbj = rw.y, ccj = rw.z;
       // grad = f (alpha (A(x) + B(y)) + va) + vb + cchi (g - alpha f - beta)
       //      = e_x e_y (K1 + alpha B(y)) + cchi g + K2
-      {
-        const float dy = (float)lane - ra.y;
-        const float e = lane < Hj ? __expf(-0.5f * dy * dy * ra.w) : 0.f;
-        rowb[lane] = make_float2(e, alj * dy * fmaf(rv.w, dy, rv.y));
+      float2 *const tb = rowb + h * 32;
+      for (int r = ln; r < 32; r += L) {
+        const float dy = (float)r - ra.y;
+        const float e = r < Hj ? __expf(-0.5f * dy * dy * ra.w) : 0.f;
+        tb[r] = make_float2(e, alj * dy * fmaf(rv.w, dy, rv.y));
       }
       __syncwarp();
+      const int yo = (int)(((float)ln + 0.5f) * rb.y);
+      const int xl = ln - yo * Wj;
+      const bool plane = yo < rpsj;
+      const int nv = plane && yo < Hj ? (int)(((float)(Hj - yo - 1) + 0.5f) / (float)rpsj) + 1 : 0;
+      const int nmax = pair ? max(nrj, __shfl_xor_sync(0xffffffffu, nrj, 16)) : nrj;
+      const bool fast = __all_sync(0xffffffffu, fullj && nrj == nmax);
       const float dx = (float)xl - ra.x;
       const float ex = __expf(-0.5f * dx * dx * ra.z);
       const float K1 = fmaf(alj, dx * fmaf(rv.z, dx, rv.x), vaj) - ccj * alj;
       const float K2 = fmaf(-ccj, betaj, vbj);
       {
-        const int nv = plane ? (Hj - yo + rpsj - 1) / rpsj : 0;
         const int step = rpsj * Wj;
         const T *p = pj + (yo * Wj + xl);
         float *q = gj + (yo * Wj + xl);
-        const float2 *rt = rowb + yo;
+        const float2 *rt = tb + yo;
         int t0 = 0;
-        if (fullj)
-          for (; t0 + kChunk <= nrj; t0 += kChunk)
-            rows_b<T, false>(p + t0 * 32, q + t0 * 32, 32, rt + t0 * rpsj, rpsj, 0, ex, K1, ccj,
-                             K2, drop);
-        for (; t0 < nrj; t0 += kChunk)
-          rows_b<T, true>(p + t0 * step, q + t0 * step, step, rt + t0 * rpsj, rpsj, nv - t0, ex,
-                          K1, ccj, K2, drop);
+        if (fast) {
+          if (pair)
+            for (; t0 + kChunk <= nmax; t0 += kChunk)
+              rows_b<T, false, 16>(p + t0 * 16, q + t0 * 16, 16, rt + t0 * rpsj, rpsj, 0, ex, K1,
+                                   ccj, K2, drop);
+          else
+            for (; t0 + kChunk <= nmax; t0 += kChunk)
+              rows_b<T, false, 32>(p + t0 * 32, q + t0 * 32, 32, rt + t0 * rpsj, rpsj, 0, ex, K1,
+                                   ccj, K2, drop);
+        }
+        for (; t0 < nmax; t0 += kChunk)
+          rows_b<T, true, 0>(p + t0 * step, q + t0 * step, step, rt + t0 * rpsj, rpsj, nv - t0,
+                             ex, K1, ccj, K2, drop);
       }
       __syncwarp();
+      j += pair ? 2 : 1;
     }
     __syncwarp();
   }

@@ -386,7 +386,7 @@ def _extra_mixed(args, dev, stream) -> dict:
     # autotuned: every usable configuration timed per size class on a 4,096-spot sample
     from paper_2106_02045_gb300 import autotune
     t0 = time.perf_counter()
-    tuned = autotune.autotune(n=4096, reps=2, dtype=fitspots.F32, device=dev)
+    tuned = autotune.autotune(n=65536, reps=2, dtype=fitspots.F32, device=dev)
     tune_s = time.perf_counter() - t0
     ams = _timed(lambda: fitspots.fit_batch(mb, out=mo, workspace=mws, stream=stream), 3, stream)
     aconv = int(torch.isin(mo["state"], torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())

@@ -217,7 +217,11 @@ int fit_spots_last_cuda_error(void);
  * 3..32. Each class runs one kernel configuration: `lanes` threads per spot (4, 8, 16
  * or 32), `cols` ROI columns held by each thread (lanes*cols covers the class's width
  * bound and stays below the next one), and the class's row bound (8, 16, 24 or 32) as
- * the per-thread row count. fit_spots_num_configs / fit_spots_config_info
+ * the per-thread row count. lanes = 1, cols = 32 is the batched kernel: each lane runs the
+ * LM step of its own spot (16 spots in flight per warp) and the warp evaluates the spots
+ * one after another, one column per thread, re-reading the pixels at each evaluation; its
+ * results are bit-identical to lanes = 32, cols = 1 at the same row bound.
+ * fit_spots_num_configs / fit_spots_config_info
  * enumerate the compiled configurations; fit_spots_set_config assigns one to a class
  * (the autotuner's output) and fails with FS_ERR_ARG if it cannot hold the class.
  */

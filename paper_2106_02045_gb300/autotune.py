@@ -9,7 +9,9 @@ sample of each class (the class's bound size, so the whole class fits it), keeps
 fastest with ``fitspots.set_config`` and can cache the choice per device.
 
 Timing uses CUDA events around ``fit_spots_uniform`` launches on the current stream;
-the sample stays resident on the device. Results of a spot depend on the configuration
+the sample stays resident on the device. The sample must fill the GPU for every candidate:
+the batched configuration (one lane per spot) keeps 16 spots per warp in flight, about
+58,000 on a 152-SM GPU, so samples much smaller than that favour the per-spot kernels. Results of a spot depend on the configuration
 only through the order of FP32 sums (within the parity tolerances either way).
 """
 from __future__ import annotations
@@ -58,7 +60,7 @@ def _time_uniform(b: synth.SpotBatch, W: int, H: int, reps: int) -> float:
     return best
 
 
-def autotune(classes=None, n: int = 8192, reps: int = 3, dtype: int = fitspots.F32,
+def autotune(classes=None, n: int = 65536, reps: int = 3, dtype: int = fitspots.F32,
              device="cuda:0", cache: str | Path | None = None, seed: int = 20210610) -> dict:
     """Time every usable configuration of each class; keep and return the fastest.
 
@@ -120,7 +122,7 @@ def defaults() -> None:
 
 
 def default_config(cls: int) -> int:
-    lanes_cols = {8: (8, 1), 16: (16, 1), 24: (8, 3), 32: (32, 1)}
+    lanes_cols = {8: (8, 1), 16: (16, 1), 24: (8, 3), 32: (1, 32)}
     L, C = lanes_cols[class_bounds(cls)[0]]
     for cfg, (l, c, r) in enumerate(fitspots.configs()):
         if (l, c, r) == (L, C, class_bounds(cls)[1]):

@@ -785,10 +785,618 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, Cla
   }
 }
 
+// ------------------------------------------------------------------ batched fit loop
+// Configuration (1, 32, R): one lane per spot for the LM step, the whole warp for the pixel
+// passes of one spot at a time. A warp keeps kSlots spots in flight. Each round it evaluates
+// every active spot at its trial point, one after another (lane = column, the arithmetic and
+// the reduction order of the (32, 1, R) configuration), then lane j runs the LM step of slot
+// j from that evaluation's sums and refills the slot when its spot finishes. The scalar LM
+// work thus runs once per 16 spots instead of once per spot. Pixels are re-read from global
+// memory (mostly L2) at each evaluation; slot state and evaluation results live in shared
+// memory.
+constexpr int kSlots = 16;
+// slot state (floats; integer fields stored as bits)
+enum : int {
+  SP = 0,        // best point p[4]
+  SPE = 4,       // trial point pe[4]
+  SDL = 8,       // last step dl[4]
+  SA = 12,       // normal matrix A[10]
+  SBV = 22,      // gradient b[4]
+  SCHIB = 26,    // chi^2 at p
+  SALB = 27,     // alpha at p
+  SBPB = 28,     // beta - shift at p
+  SNOISEB = 29,  // chi^2 error estimate at p
+  SSH0 = 30,     // integer pixel shift (corner pixel, then moved to the nearest of beta)
+  SDL0 = 31,     // (unused)
+  SGS = 32,      // sum of shifted pixels
+  SKLAM = 33, SIT = 34, SEVALS = 35, SSPOT = 36, SOFFLO = 37, SOFFHI = 38,
+  SFLAGS = 39,   // W | H << 8 | iso << 16 | first_eval << 17 | first_trial << 18 | active << 19
+  kSlotFields = 40
+};
+// evaluation results handed from the warp to the slot's lane
+enum : int { RALPHA = 0, RBP, RCHI, RNOISE, RDELTA, RT1, RT2 = RT1 + K1, kResFields = RT2 + K2 };
+constexpr int kFirstEval = 1 << 17, kFirstTrial = 1 << 18, kActive = 1 << 19;
+
+__host__ __device__ constexpr int batched_warp_floats(int R) {
+  return round_up((kSlotFields + kResFields) * kSlots, 32) + warp_smem_floats(32, R);
+}
+
+// Pixels of one spot minus a shift, one column per lane: exact for uint16 pixels (the
+// value is built as 2^23 + g in the float's mantissa, then 2^23 + shift is subtracted; both
+// are integers below 2^24); padding rows and columns are 0. `full` (W = 32, H = R) skips
+// the padding tests.
+template <int R>
+__device__ __forceinline__ void load_shifted(const FitArgs &a, int64_t off, int W, int H, int x,
+                                             bool full, float shift, float (&g)[R]) {
+  if (a.dtype == FS_U16) {
+    const unsigned short *img = static_cast<const unsigned short *>(a.images) + off;
+    const float k = 8388608.f + shift;
+    if (full) {
+#pragma unroll
+      for (int y = 0; y < R; ++y)
+        g[y] = __int_as_float(0x4b000000 | (int)__ldg(img + y * 32 + x)) - k;
+    } else {
+#pragma unroll
+      for (int y = 0; y < R; ++y)
+        g[y] = (x < W && y < H) ? __int_as_float(0x4b000000 | (int)__ldg(img + y * W + x)) - k
+                                : 0.f;
+    }
+  } else {
+    const float *img = static_cast<const float *>(a.images) + off;
+    if (full) {
+#pragma unroll
+      for (int y = 0; y < R; ++y) g[y] = __ldg(img + y * 32 + x) - shift;
+    } else {
+#pragma unroll
+      for (int y = 0; y < R; ++y) g[y] = (x < W && y < H) ? __ldg(img + y * W + x) - shift : 0.f;
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel_batched(FitArgs a, ClassList cl) {
+  constexpr int L = 32;
+  constexpr int TS2 = 2 * R + 2;
+  constexpr int RS = red_stride(L);
+  constexpr float yc0 = 0.5f * (float)R;
+  constexpr unsigned full = 0xffffffffu;
+  extern __shared__ float4 smem4[];
+  float *const sw = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * batched_warp_floats(R);
+  float *const st = sw;                                  // [kSlotFields][kSlots]
+  float *const res = sw + kSlotFields * kSlots;          // [kResFields][kSlots]
+  float *const pw = sw + round_up((kSlotFields + kResFields) * kSlots, 32);  // pass area
+  float *const tab = pw;
+  float2 *const rtab = reinterpret_cast<float2 *>(pw + tab_floats(L, R));
+  float *const red = pw + tab_floats(L, R) + rtab_floats(L, R);
+  float *const tot1 = red + K1 * RS;
+  float *const tot2 = tot1 + 20;
+  float *const tot3 = tot2 + 8;
+  (void)TS2;
+  const int lane = threadIdx.x & 31;
+  const int lg = lane;
+#define ST(f, j) st[(f) * kSlots + (j)]
+#define STI(f, j) (*reinterpret_cast<int *>(&st[(f) * kSlots + (j)]))
+#define RES(f, j) res[(f) * kSlots + (j)]
+
+  for (int ci = 0; ci < cl.count; ++ci) {
+    const int cls = cl.cls[ci];
+    const int cnt = a.uniform ? a.n : a.counts[cls];
+    const int beg = a.uniform ? 0 : a.starts[cls];
+    // lane j < kSlots owns slot j: its activity and whether the class has run dry for it
+    bool active = false, idle = lane >= kSlots || cnt == 0;
+    if (lane < kSlots) STI(SFLAGS, lane) = 0;
+    __syncwarp();
+    while (true) {
+      // -------------------------------------------------------------- refill free slots
+      {
+        const bool need = !active && !idle;
+        const unsigned m = __ballot_sync(full, need);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(a.cursors + cls, __popc(m));
+          base = __shfl_sync(full, base, leader);
+          if (need) {
+            const int item = base + __popc(m & ((1u << lane) - 1u));
+            if (item >= cnt) {
+              idle = true;
+            } else {
+              int spot, W, H, mod;
+              int64_t off;
+              if (a.uniform) {
+                spot = item;
+                off = (int64_t)item * (a.uw * a.uh);
+                W = a.uw;
+                H = a.uh;
+                mod = a.umodel;
+              } else {
+                spot = a.perm[beg + item];
+                off = a.offsets[spot];
+                W = a.dims[2 * spot];
+                H = a.dims[2 * spot + 1];
+                mod = a.model[spot];
+              }
+              const bool iso = mod == FS_MODEL_ISO;
+              float pe[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) pe[k] = a.init[4 * spot + k];
+              limit_params(pe, W, H, iso);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) ST(SPE + k, lane) = pe[k];
+              STI(SKLAM, lane) = -2;
+              STI(SIT, lane) = 0;
+              STI(SEVALS, lane) = 0;
+              STI(SSPOT, lane) = spot;
+              STI(SOFFLO, lane) = (int)(off & 0xffffffff);
+              STI(SOFFHI, lane) = (int)(off >> 32);
+              STI(SFLAGS, lane) = W | (H << 8) | ((int)iso << 16) | kFirstEval | kActive;
+              active = true;
+            }
+          }
+        }
+      }
+      const unsigned amask = __ballot_sync(full, active);
+      if (!amask) break;
+      __syncwarp();
+
+      // -------------------------------------------------------------- evaluate each slot
+      for (unsigned rem = amask; rem; rem &= rem - 1) {
+        const int j = __ffs(rem) - 1;
+        const int flags = STI(SFLAGS, j);
+        const int W = flags & 255, H = (flags >> 8) & 255;
+        const bool iso = (flags >> 16) & 1, first_eval = (flags >> 17) & 1;
+        const int64_t off =
+            (int64_t)(((uint64_t)(uint32_t)STI(SOFFHI, j) << 32) | (uint32_t)STI(SOFFLO, j));
+        const bool fullroi = W == 32 && H == R;
+        const float Nf = (float)(W * H);
+        float pe[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pe[k] = ST(SPE + k, j);
+        const int x = lg;
+        float g[R];
+        float shift, Gs;
+        if (first_eval) {
+          // integer shift = corner pixel (a background estimate); refined after pass 1
+          load_shifted<R>(a, off, W, H, x, fullroi, 0.f, g);
+          shift = rintf(__shfl_sync(full, g[0], 0));
+          float part = 0.f;
+#pragma unroll
+          for (int y = 0; y < R; ++y) {
+            g[y] = (x < W && y < H) ? g[y] - shift : 0.f;
+            part += g[y];
+          }
+          Gs = group_sum_shfl<L>(part, full);
+        } else {
+          shift = ST(SSH0, j);
+          Gs = ST(SGS, j);
+          load_shifted<R>(a, off, W, H, x, fullroi, shift, g);
+        }
+
+        const float sx = pe[2], sy = iso ? pe[2] : pe[3];
+        const float ivx = inv_sq(sx), ivy = inv_sq(sy);
+        const float nhx = -0.5f * ivx, nhy = -0.5f * ivy;
+        float ex, dxv;
+        {
+          // column profile e_x and the column moments sum dx^m e_x^n (the per-spot kernel's
+          // accumulation, one column per lane)
+          float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          const float d = (float)x - pe[0];
+          const float e = (x < W) ? __expf(d * d * nhx) : 0.f;
+          ex = e;
+          dxv = d;
+          const float e2 = e * e, de = d * e, de2 = d * e2;
+          m[0] += e;
+          m[1] += e2;
+          m[2] += de;
+          m[3] = fmaf(d, de, m[3]);
+          m[4] += de2;
+          m[5] = fmaf(d, de2, m[5]);
+          m[6] = fmaf(d * d, de2, m[6]);
+          m[7] = fmaf(d * d * d, de2, m[7]);
+          red[1 * RS + lg] = m[0];
+          red[2 * RS + lg] = m[1];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) red[(5 + k) * RS + lg] = m[2 + k];
+        }
+        {
+          // row profile e_y into the table, and the row moments
+          float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          const int y = lg;
+          if (y < R) {
+            const float d = (float)y - pe[1];
+            const float e = (y < H) ? __expf(d * d * nhy) : 0.f;
+            tab[y] = e;
+            const float e2 = e * e, de = d * e, de2 = d * e2;
+            m[0] += e;
+            m[1] += e2;
+            m[2] += de;
+            m[3] = fmaf(d, de, m[3]);
+            m[4] += de2;
+            m[5] = fmaf(d, de2, m[5]);
+            m[6] = fmaf(d * d, de2, m[6]);
+            m[7] = fmaf(d * d * d, de2, m[7]);
+          }
+          red[3 * RS + lg] = m[0];
+          red[4 * RS + lg] = m[1];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) red[(11 + k) * RS + lg] = m[2 + k];
+        }
+        __syncwarp();
+        // pass 1: s(x) = sum_y e_y g'(x, y);  FG' partial = e_x s(x)
+        {
+          float s0 = 0.f;
+#pragma unroll
+          for (int y = 0; y < R; ++y) {
+            const float e = tab[y];
+            s0 = fmaf(e, g[y], s0);
+          }
+          float fg = 0.f;
+          fg = fmaf(ex, s0, fg);
+          red[lg] = fg;
+        }
+        group_reduce<L, K1>(red, tot1, lg, full);
+        const float4 t1a = reinterpret_cast<const float4 *>(tot1)[0];
+        const float FG = t1a.x, X01 = t1a.y, X02 = t1a.z, Y01 = t1a.w, Y02 = tot1[4];
+        const float F = X01 * Y01, FF = X02 * Y02;
+        const float D = fmaf(Nf, FF, -F * F);
+        const bool okD = D > 0.f && isfinite(D);
+        const float iD = __fdividef(1.f, D);
+        const float alpha = (Nf * FG - F * Gs) * iD;  // Eq. 6
+        float bp = (Gs * FF - F * FG) * iD;           // beta^ - shift
+        if (first_eval && okD) {
+          // move the shift to the integer nearest beta^ (exact for integer pixel values)
+          const float dl0 = rintf(bp);
+#pragma unroll
+          for (int y = 0; y < R; ++y) g[y] = (x < W && y < H) ? g[y] - dl0 : 0.f;
+          Gs = fmaf(-Nf, dl0, Gs);
+          shift += dl0;
+          bp -= dl0;
+        }
+        // pass 2: u = g' - alpha e_x e_y; chi_u = sum u^2; row-weighted sums of e_y u
+        {
+          const float ca = -alpha * ex;
+          float ch0 = 0.f, ch1 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll
+          for (int y = 0; y < R; ++y) {
+            const float e = tab[y];
+            const float yy = (float)y - yc0;
+            const float u = fmaf(ca, e, g[y]);
+            if (y & 1) ch1 = fmaf(u, u, ch1);
+            else ch0 = fmaf(u, u, ch0);
+            const float w = e * u;
+            t0 += w;
+            t1 = fmaf(yy, w, t1);
+            t2 = fmaf(yy * yy, w, t2);
+          }
+          float v2[K2] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          const float e = ex, d = dxv;
+          const float et0 = e * t0;
+          v2[0] += ch0 + ch1;
+          v2[1] += et0;
+          v2[2] = fmaf(d, et0, v2[2]);
+          v2[3] = fmaf(d * d, et0, v2[3]);
+          v2[4] = fmaf(e, t1, v2[4]);
+          v2[5] = fmaf(e, t2, v2[5]);
+#pragma unroll
+          for (int k = 0; k < K2; ++k) red[k * RS + lg] = v2[k];
+        }
+        group_reduce<L, K2>(red, tot2, lg, full);
+        const float chiu = tot2[0];
+        const float Su = fmaf(-alpha, F, Gs);             // sum u = G' - alpha F
+        float chi = chiu - 2.f * bp * Su + Nf * bp * bp;  // Eq. 2: sum (u - beta')^2
+        if (!okD || !isfinite(alpha)) chi = __int_as_float(0x7fc00000);
+
+        // chi^2 change, refined near the decision thresholds (as in the per-spot kernel)
+        const float noise =
+            24.f * 5.9604645e-8f * fabsf(alpha) * sqrtf(fmaxf(chi, 0.f) * FF * __fdividef(1.f, Nf));
+        const float chib = ST(SCHIB, j), noiseb = ST(SNOISEB, j);
+        float delta = chi - chib;
+        const float win = kTieWindow * chib + noise + noiseb;
+        if (!first_eval && isfinite(chi) && isfinite(chib) && delta >= -a.min_delta * chib - win &&
+            delta <= win) {
+          float p[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) p[k] = ST(SP + k, j);
+          const float alb = ST(SALB, j), bpb = ST(SBPB, j);
+          const float sbx = p[2], sby = iso ? p[2] : p[3];
+          const float ivbx = inv_sq(sbx), ivby = inv_sq(sby);
+          const float nhbx = -0.5f * ivbx, nhby = -0.5f * ivby;
+          const float dsx = sx - sbx, dsy = sy - sby;
+          const float d0 = pe[0] - p[0], d1 = pe[1] - p[1];
+          const float kx = dsx * (sx + sbx) * ivx * ivbx, ky = dsy * (sy + sby) * ivy * ivby;
+          float mx, omx, exb, cab;
+          {
+            const float db = (float)x - p[0], dt = dxv;
+            const float dxe = 0.5f * fmaf(d0 * (dt + db), ivx, db * db * kx);
+            mx = (x < W) ? expm1_small(dxe) : 0.f;
+            omx = 1.f + mx;
+            exb = (x < W) ? __expf(db * db * nhbx) : 0.f;
+            cab = -alb * exb;
+          }
+          {
+            const int y = lg;
+            if (y < R) {
+              const float db = (float)y - p[1], dt = (float)y - pe[1];
+              const float dye = 0.5f * fmaf(d1 * (dt + db), ivy, db * db * ky);
+              rtab[y] = (y < H) ? make_float2(expm1_small(dye), __expf(db * db * nhby))
+                                : make_float2(0.f, 0.f);
+            }
+          }
+          __syncwarp();
+          const float dal = alpha - alb, dbp = bp - bpb;
+          float acc = 0.f;
+#pragma unroll
+          for (int y = 0; y < R; ++y) {
+            if (y < H && x < W) {
+              const float2 q = rtab[y];
+              const float fb = exb * q.y;
+              const float tt = fmaf(q.x, omx, mx);
+              const float dh = fmaf(fb, fmaf(alpha, tt, dal), dbp);
+              const float rb = fmaf(cab, q.y, g[y]) - bpb;
+              acc = fmaf(dh, fmaf(-2.f, rb, dh), acc);
+            }
+          }
+          red[lg] = acc;
+          group_reduce<L, 1>(red, tot3, lg, full);
+          delta = tot3[0];
+        }
+        // hand the results to the slot's lane
+        if (lane < 5) {
+          const float v = lane == 0 ? alpha : lane == 1 ? bp : lane == 2 ? chi : lane == 3 ? noise : delta;
+          RES(lane, j) = v;
+        }
+        if (lane < K1) RES(RT1 + lane, j) = tot1[lane];
+        if (lane < K2) RES(RT2 + lane, j) = tot2[lane];
+        if (first_eval && lane == 0) {
+          ST(SSH0, j) = shift;
+          ST(SGS, j) = Gs;
+        }
+        __syncwarp();
+      }
+
+      // -------------------------------------------------------------- LM step, lane per slot
+      if (active) {
+        const int j = lane;
+        int flags = STI(SFLAGS, j);
+        const int W = flags & 255, H = (flags >> 8) & 255;
+        const bool iso = (flags >> 16) & 1;
+        bool first_eval = (flags >> 17) & 1, first_trial = (flags >> 18) & 1;
+        const int P = iso ? 3 : 4;
+        const float Nf = (float)(W * H);
+        const int spot = STI(SSPOT, j);
+        float p[4], pe[4], dl[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          p[k] = ST(SP + k, j);
+          pe[k] = ST(SPE + k, j);
+          dl[k] = ST(SDL + k, j);
+        }
+        int klam = STI(SKLAM, j), it = STI(SIT, j), evals = STI(SEVALS, j) + 1;
+        float chib = ST(SCHIB, j), alb = ST(SALB, j), bpb = ST(SBPB, j), noiseb = ST(SNOISEB, j);
+        const float shift = ST(SSH0, j);
+        const float alpha = RES(RALPHA, j), bp = RES(RBP, j), chi = RES(RCHI, j);
+        const float noise = RES(RNOISE, j), delta = RES(RDELTA, j);
+
+        const float beta = bp + shift;
+        bool finish = false, need_grad = false, need_solve = false;
+        int state = FS_STATE_MAX_ITER;
+        float ra = alpha, rb = beta, rc = chi;  // values reported on finish
+        if (first_eval) {
+          first_eval = false;
+          it = 1;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) p[k] = pe[k];
+          if (isnan(chi)) {
+            finish = true;
+            state = FS_STATE_NOT_CONVERGED;
+          } else if (chi < a.max_error) {
+            finish = true;
+            state = FS_STATE_MAX_ERROR;
+          } else {
+            chib = chi;
+            alb = alpha;
+            bpb = bp;
+            noiseb = noise;
+            need_grad = true;
+          }
+        } else {
+          const float Chi = chi;
+          const bool nan_t = isnan(Chi);
+          if (first_trial && !nan_t && delta < 0.f) --klam;  // error decreased: lambda / 10
+          first_trial = false;
+          const float ms = a.min_step;
+          const bool small = fabsf(dl[0]) < ms * fabsf(p[0]) && fabsf(dl[1]) < ms * fabsf(p[1]) &&
+                             fabsf(dl[2]) < ms * fabsf(p[2]) &&
+                             (iso || fabsf(dl[3]) < ms * fabsf(p[3]));
+          if (!small && !nan_t && delta > 0.f && klam < 4) {
+            ++klam;  // reject: lambda * 10, same normal equations
+            need_solve = true;
+          } else if (nan_t || delta > 0.f) {
+            finish = true;  // keep the best point
+            state = (small && !nan_t) ? FS_STATE_NO_DECREASE : FS_STATE_NOT_CONVERGED;
+            ra = alb;
+            rb = bpb + shift;
+            rc = chib;
+          } else {
+            const float chi_prev = chib;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) p[k] = pe[k];
+            chib = Chi;
+            alb = alpha;
+            bpb = bp;
+            noiseb = noise;
+            if (Chi < a.max_error) {
+              finish = true;
+              state = FS_STATE_MAX_ERROR;
+            } else if (delta > -a.min_delta * chi_prev) {
+              finish = true;
+              state = FS_STATE_MIN_DELTA;
+            } else if (small) {
+              finish = true;
+              state = FS_STATE_MIN_STEP;
+            } else if (it >= a.max_iter) {
+              finish = true;
+              state = FS_STATE_MAX_ITER;
+            } else {
+              ++it;
+              need_grad = true;
+            }
+          }
+        }
+
+        float A[10], bv[4];
+        if (need_grad) {
+          // normal equations at p (= pe) from this evaluation's sums
+          const float FG = RES(RT1 + 0, j), X01 = RES(RT1 + 1, j), X02 = RES(RT1 + 2, j),
+                      Y01 = RES(RT1 + 3, j), Y02 = RES(RT1 + 4, j);
+          const float X11 = RES(RT1 + 5, j), X21 = RES(RT1 + 6, j), X12 = RES(RT1 + 7, j),
+                      X22 = RES(RT1 + 8, j), X32 = RES(RT1 + 9, j), X42 = RES(RT1 + 10, j);
+          const float Y11 = RES(RT1 + 11, j), Y21 = RES(RT1 + 12, j), Y12 = RES(RT1 + 13, j),
+                      Y22 = RES(RT1 + 14, j), Y32 = RES(RT1 + 15, j), Y42 = RES(RT1 + 16, j);
+          const float Tf = RES(RT2 + 1, j), Tx = RES(RT2 + 2, j), Txx = RES(RT2 + 3, j),
+                      Ty1 = RES(RT2 + 4, j), Ty2 = RES(RT2 + 5, j);
+          (void)FG;
+          const float F = X01 * Y01, FF = X02 * Y02;
+          const float D = fmaf(Nf, FF, -F * F);
+          const float iD = __fdividef(1.f, D);
+          const float sx = pe[2], sy = iso ? pe[2] : pe[3];
+          const float ivx = inv_sq(sx), ivy = inv_sq(sy);
+          const float eta = pe[1] - yc0;
+          const float cx = __fdividef(ivx, sx), cy = __fdividef(ivy, sy);
+          const float Sfdy = fmaf(-eta, Tf, Ty1);
+          const float Sfdy2 = Ty2 - 2.f * eta * Ty1 + eta * eta * Tf;
+          float Rd[4], D1[4], Fd[4], aa[4], bb[4];
+          Rd[0] = ivx * fmaf(-bp * X11, Y01, Tx);
+          Rd[1] = ivy * fmaf(-bp * X01, Y11, Sfdy);
+          Rd[2] = cx * fmaf(-bp * X21, Y01, Txx);
+          Rd[3] = cy * fmaf(-bp * X01, Y21, Sfdy2);
+          D1[0] = X11 * Y01 * ivx;
+          D1[1] = X01 * Y11 * ivy;
+          D1[2] = X21 * Y01 * cx;
+          D1[3] = X01 * Y21 * cy;
+          Fd[0] = X12 * Y02 * ivx;
+          Fd[1] = X02 * Y12 * ivy;
+          Fd[2] = X22 * Y02 * cx;
+          Fd[3] = X02 * Y22 * cy;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            aa[k] = (Nf * Rd[k] - alpha * (Nf * Fd[k] - F * D1[k])) * iD;
+            bb[k] = (alpha * (F * Fd[k] - FF * D1[k]) - F * Rd[k]) * iD;
+          }
+          const float a2 = alpha * alpha;
+          float Dd[10];
+          Dd[0] = X22 * Y02 * ivx * ivx;
+          Dd[1] = X12 * Y12 * ivx * ivy;
+          Dd[2] = X32 * Y02 * ivx * cx;
+          Dd[3] = X12 * Y22 * ivx * cy;
+          Dd[4] = X02 * Y22 * ivy * ivy;
+          Dd[5] = X22 * Y12 * ivy * cx;
+          Dd[6] = X02 * Y32 * ivy * cy;
+          Dd[7] = X42 * Y02 * cx * cx;
+          Dd[8] = X22 * Y22 * cx * cy;
+          Dd[9] = X02 * Y42 * cy * cy;
+          float M[10];
+          int idx = 0;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int k = r; k < 4; ++k, ++idx)
+              M[idx] = fmaf(aa[r], Rd[k], alpha * (Fd[r] * aa[k] + D1[r] * bb[k])) + a2 * Dd[idx];
+          if (iso) {
+            A[0] = M[0];
+            A[1] = M[1];
+            A[2] = M[2] + M[3];
+            A[3] = 0.f;
+            A[4] = M[4];
+            A[5] = M[5] + M[6];
+            A[6] = 0.f;
+            A[7] = M[7] + 2.f * M[8] + M[9];
+            A[8] = 0.f;
+            A[9] = 1.f;
+            bv[0] = alpha * Rd[0];
+            bv[1] = alpha * Rd[1];
+            bv[2] = alpha * (Rd[2] + Rd[3]);
+            bv[3] = 0.f;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) A[k] = M[k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) bv[k] = alpha * Rd[k];
+          }
+#pragma unroll
+          for (int k = 0; k < 10; ++k) ST(SA + k, j) = A[k];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) ST(SBV + k, j) = bv[k];
+          first_trial = true;
+          need_solve = true;
+        } else if (need_solve) {
+#pragma unroll
+          for (int k = 0; k < 10; ++k) A[k] = ST(SA + k, j);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) bv[k] = ST(SBV + k, j);
+        }
+        if (need_solve) {
+          float d[4];
+          if (solve_damped(A, bv, pow10i(klam), d)) {
+            if (iso) d[3] = d[2];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              dl[k] = d[k];
+              pe[k] = p[k] + d[k];
+            }
+            limit_params(pe, W, H, iso);
+          } else {
+            finish = true;
+            state = FS_STATE_NOT_CONVERGED;
+            ra = alb;
+            rb = bpb + shift;
+            rc = chib;
+          }
+        }
+        if (finish) {
+          a.out_params[4 * spot + 0] = p[0];
+          a.out_params[4 * spot + 1] = p[1];
+          a.out_params[4 * spot + 2] = p[2];
+          a.out_params[4 * spot + 3] = iso ? p[2] : p[3];
+          a.out_alpha[spot] = ra;
+          a.out_beta[spot] = rb;
+          a.out_chi2[spot] = rc / (Nf - (float)(P + 2));
+          a.out_state[spot] = state;
+          a.out_iters[spot] = it;
+          if (a.out_evals) a.out_evals[spot] = evals;
+          active = false;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          ST(SP + k, j) = p[k];
+          ST(SPE + k, j) = pe[k];
+          ST(SDL + k, j) = dl[k];
+        }
+        STI(SKLAM, j) = klam;
+        STI(SIT, j) = it;
+        STI(SEVALS, j) = evals;
+        ST(SCHIB, j) = chib;
+        ST(SALB, j) = alb;
+        ST(SBPB, j) = bpb;
+        ST(SNOISEB, j) = noiseb;
+        flags = (flags & 0x1ffff) | (first_eval ? kFirstEval : 0) | (first_trial ? kFirstTrial : 0) |
+                (active ? kActive : 0);
+        STI(SFLAGS, j) = flags;
+      }
+      __syncwarp();
+    }
+  }
+#undef ST
+#undef STI
+#undef RES
+}
+
 // ------------------------------------------------------------------ configurations
 // id -> (L, C, R); one kernel instantiation each. For every row bound R, the width
 // bound 8 has (4,2) (8,1); 16 has (4,4) (8,2) (16,1); 24 has (8,3); 32 has (8,4) (16,2)
 // (32,1).
+// L = 1 marks the batched kernel (one lane per spot for the LM step, 32 columns per pass),
+// ids 36..39 for R = 8, 16, 24, 32.
 struct CfgDesc {
   int L, C, R;
 };
@@ -797,19 +1405,27 @@ struct CfgDesc {
   X(b + 5, 8, 3, R) X(b + 6, 8, 4, R) X(b + 7, 16, 2, R) X(b + 8, 32, 1, R)
 #define FS_CONFIGS(X) \
   FS_CONFIGS_R(X, 0, 8) FS_CONFIGS_R(X, 9, 16) FS_CONFIGS_R(X, 18, 24) FS_CONFIGS_R(X, 27, 32)
+#define FS_BATCHED(X) X(36, 8) X(37, 16) X(38, 24) X(39, 32)
 
 #define FS_DESC(id, L, C, R) {L, C, R},
-constexpr CfgDesc kConfigs[] = {FS_CONFIGS(FS_DESC)};
+#define FS_BDESC(id, R) {1, 32, R},
+constexpr CfgDesc kConfigs[] = {FS_CONFIGS(FS_DESC) FS_BATCHED(FS_BDESC)};
 #undef FS_DESC
+#undef FS_BDESC
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 typedef void (*FitKernelFn)(FitArgs, ClassList);
 #define FS_PTR(id, L, C, R) &fit_kernel<L, C, R>,
-const FitKernelFn kKernels[] = {FS_CONFIGS(FS_PTR)};
+#define FS_BPTR(id, R) &fit_kernel_batched<R>,
+const FitKernelFn kKernels[] = {FS_CONFIGS(FS_PTR) FS_BATCHED(FS_BPTR)};
 #undef FS_PTR
+#undef FS_BPTR
+static_assert(sizeof(kKernels) / sizeof(kKernels[0]) == kNumConfigs, "one kernel per configuration");
 
 size_t config_smem_bytes(int cfg) {
-  return (size_t)kWarpsPerBlock * warp_smem_floats(kConfigs[cfg].L, kConfigs[cfg].R) * sizeof(float);
+  const int R = kConfigs[cfg].R;
+  const int per_warp = kConfigs[cfg].L == 1 ? batched_warp_floats(R) : warp_smem_floats(kConfigs[cfg].L, R);
+  return (size_t)kWarpsPerBlock * per_warp * sizeof(float);
 }
 
 // ------------------------------------------------------------------ schedule prepass
@@ -891,7 +1507,8 @@ bool config_fits(int cfg, int cls) {
 }
 
 void init_defaults() {
-  static const int lc[4][2] = {{8, 1}, {16, 1}, {8, 3}, {32, 1}};  // by width bound 8..32
+  // by width bound 8..32; (1, 32) is the batched kernel
+  static const int lc[4][2] = {{8, 1}, {16, 1}, {8, 3}, {1, 32}};
   for (int cls = 0; cls < kNumClasses; ++cls) {
     const int wb = cls / 4, hb = cls % 4;
     g_class_cfg[cls] = (int8_t)config_for(lc[wb][0], lc[wb][1], (hb + 1) * 8);

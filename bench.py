@@ -121,6 +121,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _kernel_name(size_class: int) -> str:
+    """The kernel a size class runs under the current configuration table."""
+    from paper_2106_02045_gb300 import fitspots
+    L, C, R = fitspots.configs()[fitspots.get_config(size_class)]
+    return f"fit_kernel_batched<{R}>" if L == 1 else f"fit_kernel<{L},{C},{R}>"
+
+
 def _traffic_from_profile(profile=None, source=None) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
     profile = PROFILE if profile is None else profile
@@ -281,7 +288,7 @@ def run(args) -> None:
                 "direct_count": {"iters_per_spot": iters / n_spots,
                                  "frac": float(evals * 12 + iters * 26) * W * H / kernel_s / peak},
                 "peak_source": f"derived: {SMS} SMs x {LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz",
-                "kernel": "fit_kernel (uniform 32x32)"}
+                "kernel": _kernel_name(15)}
     cpu = None
     if not args.no_cpu_baseline:
         bcpu = b.head(args.cpu_sample).to("cpu")

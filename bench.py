@@ -124,8 +124,8 @@ class ClockSampler:
 def _kernel_name(size_class: int) -> str:
     """The kernel a size class runs under the current configuration table."""
     from paper_2106_02045_gb300 import fitspots
-    L, C, R = fitspots.configs()[fitspots.get_config(size_class)]
-    return f"fit_kernel_batched<{R}>" if L == 1 else f"fit_kernel<{L},{C},{R}>"
+    L, C, R, batched = fitspots.configs()[fitspots.get_config(size_class)]
+    return f"fit_kernel{'_batched' if batched else ''}<{L},{C},{R}>"
 
 
 def _traffic_from_profile(profile=None, source=None) -> float | None:
@@ -393,7 +393,7 @@ def _extra_mixed(args, dev, stream) -> dict:
     # autotuned: every usable configuration timed per size class on a 4,096-spot sample
     from paper_2106_02045_gb300 import autotune
     t0 = time.perf_counter()
-    tuned = autotune.autotune(n=65536, reps=2, dtype=fitspots.F32, device=dev)
+    tuned = autotune.autotune(n=131072, reps=2, dtype=fitspots.F32, device=dev)
     tune_s = time.perf_counter() - t0
     ams = _timed(lambda: fitspots.fit_batch(mb, out=mo, workspace=mws, stream=stream), 3, stream)
     aconv = int(torch.isin(mo["state"], torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())

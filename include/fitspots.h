@@ -217,10 +217,11 @@ int fit_spots_last_cuda_error(void);
  * 3..32. Each class runs one kernel configuration: `lanes` threads per spot (4, 8, 16
  * or 32), `cols` ROI columns held by each thread (lanes*cols covers the class's width
  * bound and stays below the next one), and the class's row bound (8, 16, 24 or 32) as
- * the per-thread row count. lanes = 1, cols = 32 is the batched kernel: each lane runs the
- * LM step of its own spot (16 spots in flight per warp) and the warp evaluates the spots
- * one after another, one column per thread, re-reading the pixels at each evaluation; its
- * results are bit-identical to lanes = 32, cols = 1 at the same row bound.
+ * the per-thread row count. A configuration is per-spot (each lane group fits one spot
+ * from start to stop, every lane running the LM step) or batched
+ * (fit_spots_config_batched = 1): a warp keeps 16 spots in flight, its lane groups evaluate
+ * them with that geometry, re-reading the pixels at each evaluation, and lane j runs the LM
+ * step of spot j; per-spot and batched results of the same geometry agree to FP32 rounding.
  * fit_spots_num_configs / fit_spots_config_info
  * enumerate the compiled configurations; fit_spots_set_config assigns one to a class
  * (the autotuner's output) and fails with FS_ERR_ARG if it cannot hold the class.
@@ -228,8 +229,10 @@ int fit_spots_last_cuda_error(void);
 int fit_spots_num_classes(void);
 int fit_spots_num_configs(void);
 int fit_spots_config_info(int config, int *lanes, int *cols, int *rows);
+int fit_spots_config_batched(int config); /* 1 batched, 0 per-spot, FS_ERR_ARG if unknown */
 int fit_spots_config_fits(int size_class, int config); /* 1 if usable, else 0 */
 int fit_spots_get_config(int size_class);
+int fit_spots_default_config(int size_class); /* the built-in choice the library starts with */
 int fit_spots_set_config(int size_class, int config);
 
 #ifdef __cplusplus

@@ -1,17 +1,17 @@
 """Per-size-class kernel configuration autotuner.
 
 Every size class (ceil(W/8), ceil(H/8)) can run several compiled configurations (lanes
-per spot, columns per lane, rows): ``fitspots.configs()`` lists them and
-``fitspots.config_fits`` says which serve a class. The defaults are chosen by width
-bound alone; the best choice also depends on the GPU, the pixel type and the fit
-statistics of the data. ``autotune`` times every usable configuration on a synthetic
+per spot, columns per lane, rows, per-spot or batched): ``fitspots.configs()`` lists them and
+``fitspots.config_fits`` says which serve a class. The library's built-in defaults were
+timed on one GPU with FP32 samples; the best choice also depends on the GPU, the pixel type
+and the fit statistics of the data. ``autotune`` times every usable configuration on a synthetic
 sample of each class (the class's bound size, so the whole class fits it), keeps the
 fastest with ``fitspots.set_config`` and can cache the choice per device.
 
 Timing uses CUDA events around ``fit_spots_uniform`` launches on the current stream;
 the sample stays resident on the device. The sample must fill the GPU for every candidate:
 the batched configuration (one lane per spot) keeps 16 spots per warp in flight, about
-58,000 on a 152-SM GPU, so samples much smaller than that favour the per-spot kernels. Results of a spot depend on the configuration
+58,000 on a 152-SM GPU, so samples much smaller than twice that favour the per-spot kernels. Results of a spot depend on the configuration
 only through the order of FP32 sums (within the parity tolerances either way).
 """
 from __future__ import annotations
@@ -60,7 +60,7 @@ def _time_uniform(b: synth.SpotBatch, W: int, H: int, reps: int) -> float:
     return best
 
 
-def autotune(classes=None, n: int = 65536, reps: int = 3, dtype: int = fitspots.F32,
+def autotune(classes=None, n: int = 131072, reps: int = 3, dtype: int = fitspots.F32,
              device="cuda:0", cache: str | Path | None = None, seed: int = 20210610) -> dict:
     """Time every usable configuration of each class; keep and return the fastest.
 
@@ -122,9 +122,5 @@ def defaults() -> None:
 
 
 def default_config(cls: int) -> int:
-    lanes_cols = {8: (8, 1), 16: (16, 1), 24: (8, 3), 32: (1, 32)}
-    L, C = lanes_cols[class_bounds(cls)[0]]
-    for cfg, (l, c, r) in enumerate(fitspots.configs()):
-        if (l, c, r) == (L, C, class_bounds(cls)[1]):
-            return cfg
-    raise ValueError(f"no default configuration for class {cls}")
+    """The library's built-in configuration of a size class."""
+    return fitspots.default_config(cls)

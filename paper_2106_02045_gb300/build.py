@@ -30,6 +30,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     if not force and LIB.exists() and LIB.stat().st_mtime >= newest:
         return LIB
     tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    # no -split-compile: it made register allocation vary from build to build, with spills
     cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            f"-I{ROOT / 'include'}", "-o", str(tmp)] + [str(s) for s in SOURCES]
     if verbose:

@@ -817,63 +817,87 @@ enum : int {
 enum : int { RALPHA = 0, RBP, RCHI, RNOISE, RDELTA, RT1, RT2 = RT1 + K1, kResFields = RT2 + K2 };
 constexpr int kFirstEval = 1 << 17, kFirstTrial = 1 << 18, kActive = 1 << 19;
 
-__host__ __device__ constexpr int batched_warp_floats(int R) {
-  return round_up((kSlotFields + kResFields) * kSlots, 32) + warp_smem_floats(32, R);
+__host__ __device__ constexpr int batched_warp_floats(int L, int R) {
+  return round_up((kSlotFields + kResFields) * kSlots, 32) + warp_smem_floats(L, R);
 }
 
 // Pixels of one spot minus a shift, one column per lane: exact for uint16 pixels (the
 // value is built as 2^23 + g in the float's mantissa, then 2^23 + shift is subtracted; both
 // are integers below 2^24); padding rows and columns are 0. `full` (W = 32, H = R) skips
 // the padding tests.
-template <int R>
-__device__ __forceinline__ void load_shifted(const FitArgs &a, int64_t off, int W, int H, int x,
-                                             bool full, float shift, float (&g)[R]) {
+// Pixels of one spot minus a shift, columns lg + L c of this lane: exact for uint16 pixels
+// (the value is built as 2^23 + g in the float's mantissa, then 2^23 + shift is subtracted;
+// both are integers below 2^24); padding rows and columns are 0. `full` (W = L C, H = R)
+// skips the padding tests.
+template <int L, int C, int R>
+__device__ __forceinline__ void load_shifted(const FitArgs &a, int64_t off, int W, int H, int lg,
+                                             bool full, float shift, float (&g)[C][R]) {
   if (a.dtype == FS_U16) {
     const unsigned short *img = static_cast<const unsigned short *>(a.images) + off;
     const float k = 8388608.f + shift;
-    if (full) {
 #pragma unroll
-      for (int y = 0; y < R; ++y)
-        g[y] = __int_as_float(0x4b000000 | (int)__ldg(img + y * 32 + x)) - k;
-    } else {
+    for (int c = 0; c < C; ++c) {
+      const int x = lg + L * c;
+      if (full) {
 #pragma unroll
-      for (int y = 0; y < R; ++y)
-        g[y] = (x < W && y < H) ? __int_as_float(0x4b000000 | (int)__ldg(img + y * W + x)) - k
-                                : 0.f;
+        for (int y = 0; y < R; ++y)
+          g[c][y] = __int_as_float(0x4b000000 | (int)__ldg(img + y * (L * C) + x)) - k;
+      } else {
+#pragma unroll
+        for (int y = 0; y < R; ++y)
+          g[c][y] = (x < W && y < H) ? __int_as_float(0x4b000000 | (int)__ldg(img + y * W + x)) - k
+                                     : 0.f;
+      }
     }
   } else {
     const float *img = static_cast<const float *>(a.images) + off;
-    if (full) {
 #pragma unroll
-      for (int y = 0; y < R; ++y) g[y] = __ldg(img + y * 32 + x) - shift;
-    } else {
+    for (int c = 0; c < C; ++c) {
+      const int x = lg + L * c;
+      if (full) {
 #pragma unroll
-      for (int y = 0; y < R; ++y) g[y] = (x < W && y < H) ? __ldg(img + y * W + x) - shift : 0.f;
+        for (int y = 0; y < R; ++y) g[c][y] = __ldg(img + y * (L * C) + x) - shift;
+      } else {
+#pragma unroll
+        for (int y = 0; y < R; ++y) g[c][y] = (x < W && y < H) ? __ldg(img + y * W + x) - shift : 0.f;
+      }
     }
   }
 }
 
-template <int R>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel_batched(FitArgs a, ClassList cl) {
-  constexpr int L = 32;
-  constexpr int TS2 = 2 * R + 2;
+// Batched configuration (L, C, R): the warp's 32 / L lane groups evaluate that many slots at
+// once, each group as one spot of the per-spot kernel with the same (L, C, R).
+// Resident blocks per SM the batched kernels are compiled for: the kernel waits on L2 for
+// the pixels of every evaluation, so occupancy pays until the register file runs out; C R
+// registers hold a lane's pixels.
+__host__ __device__ constexpr int batched_min_blocks(int C, int R) {
+  return C * R <= 32 ? 6 : C * R <= 64 ? 4 : 3;
+}
+
+template <int L, int C, int R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, batched_min_blocks(C, R))
+    fit_kernel_batched(FitArgs a, ClassList cl) {
+  constexpr int S = 32 / L;
+  constexpr int NR = (R + L - 1) / L;
   constexpr int RS = red_stride(L);
   constexpr float yc0 = 0.5f * (float)R;
   constexpr unsigned full = 0xffffffffu;
+  static_assert(S * L == 32, "lane groups must tile a warp");
   extern __shared__ float4 smem4[];
-  float *const sw = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * batched_warp_floats(R);
-  float *const st = sw;                                  // [kSlotFields][kSlots]
-  float *const res = sw + kSlotFields * kSlots;          // [kResFields][kSlots]
+  float *const sw =
+      reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * batched_warp_floats(L, R);
+  float *const st = sw;                          // [kSlotFields][kSlots]
+  float *const res = sw + kSlotFields * kSlots;  // [kResFields][kSlots]
   float *const pw = sw + round_up((kSlotFields + kResFields) * kSlots, 32);  // pass area
-  float *const tab = pw;
-  float2 *const rtab = reinterpret_cast<float2 *>(pw + tab_floats(L, R));
-  float *const red = pw + tab_floats(L, R) + rtab_floats(L, R);
+  const int lane = threadIdx.x & 31;
+  const int gi = lane / L, lg = lane % L;
+  const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (gi * L));
+  float *const tab = pw + gi * (R + 1);
+  float2 *const rtab = reinterpret_cast<float2 *>(pw + tab_floats(L, R) + gi * (2 * R + 2));
+  float *const red = pw + tab_floats(L, R) + rtab_floats(L, R) + gi * group_stride(L);
   float *const tot1 = red + K1 * RS;
   float *const tot2 = tot1 + 20;
   float *const tot3 = tot2 + 8;
-  (void)TS2;
-  const int lane = threadIdx.x & 31;
-  const int lg = lane;
 #define ST(f, j) st[(f) * kSlots + (j)]
 #define STI(f, j) (*reinterpret_cast<int *>(&st[(f) * kSlots + (j)]))
 #define RES(f, j) res[(f) * kSlots + (j)]
@@ -939,73 +963,54 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel_batched(FitArg
       if (!amask) break;
       __syncwarp();
 
-      // -------------------------------------------------------------- evaluate each slot
-      for (unsigned rem = amask; rem; rem &= rem - 1) {
-        const int j = __ffs(rem) - 1;
-        const int flags = STI(SFLAGS, j);
-        const int W = flags & 255, H = (flags >> 8) & 255;
-        const bool iso = (flags >> 16) & 1, first_eval = (flags >> 17) & 1;
-        const int64_t off =
-            (int64_t)(((uint64_t)(uint32_t)STI(SOFFHI, j) << 32) | (uint32_t)STI(SOFFLO, j));
-        const bool fullroi = W == 32 && H == R;
-        const float Nf = (float)(W * H);
-        float pe[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) pe[k] = ST(SPE + k, j);
-        const int x = lg;
-        float g[R];
-        float shift, Gs;
-        if (first_eval) {
-          // integer shift = corner pixel (a background estimate); refined after pass 1
-          load_shifted<R>(a, off, W, H, x, fullroi, 0.f, g);
-          shift = rintf(__shfl_sync(full, g[0], 0));
-          float part = 0.f;
-#pragma unroll
-          for (int y = 0; y < R; ++y) {
-            g[y] = (x < W && y < H) ? g[y] - shift : 0.f;
-            part += g[y];
+      if constexpr (L == 32 && C == 1) {
+        // one spot per warp: the same steps written for a single column per lane, which
+        // keeps the kernel at 80 registers without spilling (6 blocks per SM)
+        for (unsigned rem = amask; rem; rem &= rem - 1) {
+          const int j = __ffs(rem) - 1;
+          const int flags = STI(SFLAGS, j);
+          const int W = flags & 255, H = (flags >> 8) & 255;
+          const bool iso = (flags >> 16) & 1, first_eval = (flags >> 17) & 1;
+          const int64_t off =
+              (int64_t)(((uint64_t)(uint32_t)STI(SOFFHI, j) << 32) | (uint32_t)STI(SOFFLO, j));
+          const bool fullroi = W == 32 && H == R;
+          const float Nf = (float)(W * H);
+          float pe[4];
+  #pragma unroll
+          for (int k = 0; k < 4; ++k) pe[k] = ST(SPE + k, j);
+          const int x = lg;
+          float g2[1][R];
+          float (&g)[R] = g2[0];
+          float shift, Gs;
+          if (first_eval) {
+            // integer shift = corner pixel (a background estimate); refined after pass 1
+            load_shifted<32, 1, R>(a, off, W, H, x, fullroi, 0.f, g2);
+            shift = rintf(__shfl_sync(full, g[0], 0));
+            float part = 0.f;
+  #pragma unroll
+            for (int y = 0; y < R; ++y) {
+              g[y] = (x < W && y < H) ? g[y] - shift : 0.f;
+              part += g[y];
+            }
+            Gs = group_sum_shfl<L>(part, full);
+          } else {
+            shift = ST(SSH0, j);
+            Gs = ST(SGS, j);
+            load_shifted<32, 1, R>(a, off, W, H, x, fullroi, shift, g2);
           }
-          Gs = group_sum_shfl<L>(part, full);
-        } else {
-          shift = ST(SSH0, j);
-          Gs = ST(SGS, j);
-          load_shifted<R>(a, off, W, H, x, fullroi, shift, g);
-        }
 
-        const float sx = pe[2], sy = iso ? pe[2] : pe[3];
-        const float ivx = inv_sq(sx), ivy = inv_sq(sy);
-        const float nhx = -0.5f * ivx, nhy = -0.5f * ivy;
-        float ex, dxv;
-        {
-          // column profile e_x and the column moments sum dx^m e_x^n (the per-spot kernel's
-          // accumulation, one column per lane)
-          float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          const float d = (float)x - pe[0];
-          const float e = (x < W) ? __expf(d * d * nhx) : 0.f;
-          ex = e;
-          dxv = d;
-          const float e2 = e * e, de = d * e, de2 = d * e2;
-          m[0] += e;
-          m[1] += e2;
-          m[2] += de;
-          m[3] = fmaf(d, de, m[3]);
-          m[4] += de2;
-          m[5] = fmaf(d, de2, m[5]);
-          m[6] = fmaf(d * d, de2, m[6]);
-          m[7] = fmaf(d * d * d, de2, m[7]);
-          red[1 * RS + lg] = m[0];
-          red[2 * RS + lg] = m[1];
-#pragma unroll
-          for (int k = 0; k < 6; ++k) red[(5 + k) * RS + lg] = m[2 + k];
-        }
-        {
-          // row profile e_y into the table, and the row moments
-          float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          const int y = lg;
-          if (y < R) {
-            const float d = (float)y - pe[1];
-            const float e = (y < H) ? __expf(d * d * nhy) : 0.f;
-            tab[y] = e;
+          const float sx = pe[2], sy = iso ? pe[2] : pe[3];
+          const float ivx = inv_sq(sx), ivy = inv_sq(sy);
+          const float nhx = -0.5f * ivx, nhy = -0.5f * ivy;
+          float ex, dxv;
+          {
+            // column profile e_x and the column moments sum dx^m e_x^n (the per-spot kernel's
+            // accumulation, one column per lane)
+            float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float d = (float)x - pe[0];
+            const float e = (x < W) ? __expf(d * d * nhx) : 0.f;
+            ex = e;
+            dxv = d;
             const float e2 = e * e, de = d * e, de2 = d * e2;
             m[0] += e;
             m[1] += e2;
@@ -1015,143 +1020,434 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel_batched(FitArg
             m[5] = fmaf(d, de2, m[5]);
             m[6] = fmaf(d * d, de2, m[6]);
             m[7] = fmaf(d * d * d, de2, m[7]);
-          }
-          red[3 * RS + lg] = m[0];
-          red[4 * RS + lg] = m[1];
-#pragma unroll
-          for (int k = 0; k < 6; ++k) red[(11 + k) * RS + lg] = m[2 + k];
-        }
-        __syncwarp();
-        // pass 1: s(x) = sum_y e_y g'(x, y);  FG' partial = e_x s(x)
-        {
-          float s0 = 0.f;
-#pragma unroll
-          for (int y = 0; y < R; ++y) {
-            const float e = tab[y];
-            s0 = fmaf(e, g[y], s0);
-          }
-          float fg = 0.f;
-          fg = fmaf(ex, s0, fg);
-          red[lg] = fg;
-        }
-        group_reduce<L, K1>(red, tot1, lg, full);
-        const float4 t1a = reinterpret_cast<const float4 *>(tot1)[0];
-        const float FG = t1a.x, X01 = t1a.y, X02 = t1a.z, Y01 = t1a.w, Y02 = tot1[4];
-        const float F = X01 * Y01, FF = X02 * Y02;
-        const float D = fmaf(Nf, FF, -F * F);
-        const bool okD = D > 0.f && isfinite(D);
-        const float iD = __fdividef(1.f, D);
-        const float alpha = (Nf * FG - F * Gs) * iD;  // Eq. 6
-        float bp = (Gs * FF - F * FG) * iD;           // beta^ - shift
-        if (first_eval && okD) {
-          // move the shift to the integer nearest beta^ (exact for integer pixel values)
-          const float dl0 = rintf(bp);
-#pragma unroll
-          for (int y = 0; y < R; ++y) g[y] = (x < W && y < H) ? g[y] - dl0 : 0.f;
-          Gs = fmaf(-Nf, dl0, Gs);
-          shift += dl0;
-          bp -= dl0;
-        }
-        // pass 2: u = g' - alpha e_x e_y; chi_u = sum u^2; row-weighted sums of e_y u
-        {
-          const float ca = -alpha * ex;
-          float ch0 = 0.f, ch1 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
-#pragma unroll
-          for (int y = 0; y < R; ++y) {
-            const float e = tab[y];
-            const float yy = (float)y - yc0;
-            const float u = fmaf(ca, e, g[y]);
-            if (y & 1) ch1 = fmaf(u, u, ch1);
-            else ch0 = fmaf(u, u, ch0);
-            const float w = e * u;
-            t0 += w;
-            t1 = fmaf(yy, w, t1);
-            t2 = fmaf(yy * yy, w, t2);
-          }
-          float v2[K2] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          const float e = ex, d = dxv;
-          const float et0 = e * t0;
-          v2[0] += ch0 + ch1;
-          v2[1] += et0;
-          v2[2] = fmaf(d, et0, v2[2]);
-          v2[3] = fmaf(d * d, et0, v2[3]);
-          v2[4] = fmaf(e, t1, v2[4]);
-          v2[5] = fmaf(e, t2, v2[5]);
-#pragma unroll
-          for (int k = 0; k < K2; ++k) red[k * RS + lg] = v2[k];
-        }
-        group_reduce<L, K2>(red, tot2, lg, full);
-        const float chiu = tot2[0];
-        const float Su = fmaf(-alpha, F, Gs);             // sum u = G' - alpha F
-        float chi = chiu - 2.f * bp * Su + Nf * bp * bp;  // Eq. 2: sum (u - beta')^2
-        if (!okD || !isfinite(alpha)) chi = __int_as_float(0x7fc00000);
-
-        // chi^2 change, refined near the decision thresholds (as in the per-spot kernel)
-        const float noise =
-            24.f * 5.9604645e-8f * fabsf(alpha) * sqrtf(fmaxf(chi, 0.f) * FF * __fdividef(1.f, Nf));
-        const float chib = ST(SCHIB, j), noiseb = ST(SNOISEB, j);
-        float delta = chi - chib;
-        const float win = kTieWindow * chib + noise + noiseb;
-        if (!first_eval && isfinite(chi) && isfinite(chib) && delta >= -a.min_delta * chib - win &&
-            delta <= win) {
-          float p[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) p[k] = ST(SP + k, j);
-          const float alb = ST(SALB, j), bpb = ST(SBPB, j);
-          const float sbx = p[2], sby = iso ? p[2] : p[3];
-          const float ivbx = inv_sq(sbx), ivby = inv_sq(sby);
-          const float nhbx = -0.5f * ivbx, nhby = -0.5f * ivby;
-          const float dsx = sx - sbx, dsy = sy - sby;
-          const float d0 = pe[0] - p[0], d1 = pe[1] - p[1];
-          const float kx = dsx * (sx + sbx) * ivx * ivbx, ky = dsy * (sy + sby) * ivy * ivby;
-          float mx, omx, exb, cab;
-          {
-            const float db = (float)x - p[0], dt = dxv;
-            const float dxe = 0.5f * fmaf(d0 * (dt + db), ivx, db * db * kx);
-            mx = (x < W) ? expm1_small(dxe) : 0.f;
-            omx = 1.f + mx;
-            exb = (x < W) ? __expf(db * db * nhbx) : 0.f;
-            cab = -alb * exb;
+            red[1 * RS + lg] = m[0];
+            red[2 * RS + lg] = m[1];
+  #pragma unroll
+            for (int k = 0; k < 6; ++k) red[(5 + k) * RS + lg] = m[2 + k];
           }
           {
+            // row profile e_y into the table, and the row moments
+            float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int y = lg;
             if (y < R) {
-              const float db = (float)y - p[1], dt = (float)y - pe[1];
-              const float dye = 0.5f * fmaf(d1 * (dt + db), ivy, db * db * ky);
-              rtab[y] = (y < H) ? make_float2(expm1_small(dye), __expf(db * db * nhby))
-                                : make_float2(0.f, 0.f);
+              const float d = (float)y - pe[1];
+              const float e = (y < H) ? __expf(d * d * nhy) : 0.f;
+              tab[y] = e;
+              const float e2 = e * e, de = d * e, de2 = d * e2;
+              m[0] += e;
+              m[1] += e2;
+              m[2] += de;
+              m[3] = fmaf(d, de, m[3]);
+              m[4] += de2;
+              m[5] = fmaf(d, de2, m[5]);
+              m[6] = fmaf(d * d, de2, m[6]);
+              m[7] = fmaf(d * d * d, de2, m[7]);
+            }
+            red[3 * RS + lg] = m[0];
+            red[4 * RS + lg] = m[1];
+  #pragma unroll
+            for (int k = 0; k < 6; ++k) red[(11 + k) * RS + lg] = m[2 + k];
+          }
+          __syncwarp();
+          // pass 1: s(x) = sum_y e_y g'(x, y);  FG' partial = e_x s(x)
+          {
+            float s0 = 0.f;
+  #pragma unroll
+            for (int y = 0; y < R; ++y) {
+              const float e = tab[y];
+              s0 = fmaf(e, g[y], s0);
+            }
+            float fg = 0.f;
+            fg = fmaf(ex, s0, fg);
+            red[lg] = fg;
+          }
+          group_reduce<L, K1>(red, tot1, lg, full);
+          const float4 t1a = reinterpret_cast<const float4 *>(tot1)[0];
+          const float FG = t1a.x, X01 = t1a.y, X02 = t1a.z, Y01 = t1a.w, Y02 = tot1[4];
+          const float F = X01 * Y01, FF = X02 * Y02;
+          const float D = fmaf(Nf, FF, -F * F);
+          const bool okD = D > 0.f && isfinite(D);
+          const float iD = __fdividef(1.f, D);
+          const float alpha = (Nf * FG - F * Gs) * iD;  // Eq. 6
+          float bp = (Gs * FF - F * FG) * iD;           // beta^ - shift
+          if (first_eval && okD) {
+            // move the shift to the integer nearest beta^ (exact for integer pixel values)
+            const float dl0 = rintf(bp);
+  #pragma unroll
+            for (int y = 0; y < R; ++y) g[y] = (x < W && y < H) ? g[y] - dl0 : 0.f;
+            Gs = fmaf(-Nf, dl0, Gs);
+            shift += dl0;
+            bp -= dl0;
+          }
+          // pass 2: u = g' - alpha e_x e_y; chi_u = sum u^2; row-weighted sums of e_y u
+          {
+            const float ca = -alpha * ex;
+            float ch0 = 0.f, ch1 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
+  #pragma unroll
+            for (int y = 0; y < R; ++y) {
+              const float e = tab[y];
+              const float yy = (float)y - yc0;
+              const float u = fmaf(ca, e, g[y]);
+              if (y & 1) ch1 = fmaf(u, u, ch1);
+              else ch0 = fmaf(u, u, ch0);
+              const float w = e * u;
+              t0 += w;
+              t1 = fmaf(yy, w, t1);
+              t2 = fmaf(yy * yy, w, t2);
+            }
+            float v2[K2] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float e = ex, d = dxv;
+            const float et0 = e * t0;
+            v2[0] += ch0 + ch1;
+            v2[1] += et0;
+            v2[2] = fmaf(d, et0, v2[2]);
+            v2[3] = fmaf(d * d, et0, v2[3]);
+            v2[4] = fmaf(e, t1, v2[4]);
+            v2[5] = fmaf(e, t2, v2[5]);
+  #pragma unroll
+            for (int k = 0; k < K2; ++k) red[k * RS + lg] = v2[k];
+          }
+          group_reduce<L, K2>(red, tot2, lg, full);
+          const float chiu = tot2[0];
+          const float Su = fmaf(-alpha, F, Gs);             // sum u = G' - alpha F
+          float chi = chiu - 2.f * bp * Su + Nf * bp * bp;  // Eq. 2: sum (u - beta')^2
+          if (!okD || !isfinite(alpha)) chi = __int_as_float(0x7fc00000);
+
+          // chi^2 change, refined near the decision thresholds (as in the per-spot kernel)
+          const float noise =
+              24.f * 5.9604645e-8f * fabsf(alpha) * sqrtf(fmaxf(chi, 0.f) * FF * __fdividef(1.f, Nf));
+          const float chib = ST(SCHIB, j), noiseb = ST(SNOISEB, j);
+          float delta = chi - chib;
+          const float win = kTieWindow * chib + noise + noiseb;
+          if (!first_eval && isfinite(chi) && isfinite(chib) && delta >= -a.min_delta * chib - win &&
+              delta <= win) {
+            float p[4];
+  #pragma unroll
+            for (int k = 0; k < 4; ++k) p[k] = ST(SP + k, j);
+            const float alb = ST(SALB, j), bpb = ST(SBPB, j);
+            const float sbx = p[2], sby = iso ? p[2] : p[3];
+            const float ivbx = inv_sq(sbx), ivby = inv_sq(sby);
+            const float nhbx = -0.5f * ivbx, nhby = -0.5f * ivby;
+            const float dsx = sx - sbx, dsy = sy - sby;
+            const float d0 = pe[0] - p[0], d1 = pe[1] - p[1];
+            const float kx = dsx * (sx + sbx) * ivx * ivbx, ky = dsy * (sy + sby) * ivy * ivby;
+            float mx, omx, exb, cab;
+            {
+              const float db = (float)x - p[0], dt = dxv;
+              const float dxe = 0.5f * fmaf(d0 * (dt + db), ivx, db * db * kx);
+              mx = (x < W) ? expm1_small(dxe) : 0.f;
+              omx = 1.f + mx;
+              exb = (x < W) ? __expf(db * db * nhbx) : 0.f;
+              cab = -alb * exb;
+            }
+            {
+              const int y = lg;
+              if (y < R) {
+                const float db = (float)y - p[1], dt = (float)y - pe[1];
+                const float dye = 0.5f * fmaf(d1 * (dt + db), ivy, db * db * ky);
+                rtab[y] = (y < H) ? make_float2(expm1_small(dye), __expf(db * db * nhby))
+                                  : make_float2(0.f, 0.f);
+              }
+            }
+            __syncwarp();
+            const float dal = alpha - alb, dbp = bp - bpb;
+            float acc = 0.f;
+  #pragma unroll
+            for (int y = 0; y < R; ++y) {
+              if (y < H && x < W) {
+                const float2 q = rtab[y];
+                const float fb = exb * q.y;
+                const float tt = fmaf(q.x, omx, mx);
+                const float dh = fmaf(fb, fmaf(alpha, tt, dal), dbp);
+                const float rb = fmaf(cab, q.y, g[y]) - bpb;
+                acc = fmaf(dh, fmaf(-2.f, rb, dh), acc);
+              }
+            }
+            red[lg] = acc;
+            group_reduce<L, 1>(red, tot3, lg, full);
+            delta = tot3[0];
+          }
+          // hand the results to the slot's lane
+          if (lane < 5) {
+            const float v = lane == 0 ? alpha : lane == 1 ? bp : lane == 2 ? chi : lane == 3 ? noise : delta;
+            RES(lane, j) = v;
+          }
+          if (lane < K1) RES(RT1 + lane, j) = tot1[lane];
+          if (lane < K2) RES(RT2 + lane, j) = tot2[lane];
+          if (first_eval && lane == 0) {
+            ST(SSH0, j) = shift;
+            ST(SGS, j) = Gs;
+          }
+          __syncwarp();
+        }
+      } else {
+        // -------------------------------------------------------------- evaluate the slots,
+        // S at a time (group gi takes the gi-th remaining active slot)
+        for (unsigned rem = amask; rem;) {
+          unsigned r = rem;
+  #pragma unroll
+          for (int k = 0; k < S - 1; ++k)
+            if (k < gi) r &= r - 1;
+  #pragma unroll
+          for (int k = 0; k < S; ++k) rem &= rem - 1;
+          if (r) {
+            const int j = __ffs(r) - 1;
+            const int flags = STI(SFLAGS, j);
+            const int W = flags & 255, H = (flags >> 8) & 255;
+            const bool iso = (flags >> 16) & 1;
+            bool first_eval = (flags >> 17) & 1;
+            const int64_t off =
+                (int64_t)(((uint64_t)(uint32_t)STI(SOFFHI, j) << 32) | (uint32_t)STI(SOFFLO, j));
+            const float Nf = (float)(W * H);
+            float pe[4];
+  #pragma unroll
+            for (int k = 0; k < 4; ++k) pe[k] = ST(SPE + k, j);
+            float g[C][R];
+            float shift, Gs;
+            if (first_eval) {
+              // integer shift = corner pixel (a background estimate); refined after pass 1
+              load_shifted<L, C, R>(a, off, W, H, lg, false, 0.f, g);
+              shift = rintf(__shfl_sync(gmask, g[0][0], gi * L));
+              float part = 0.f;
+  #pragma unroll
+              for (int c = 0; c < C; ++c) {
+                const int x = lg + L * c;
+  #pragma unroll
+                for (int y = 0; y < R; ++y) {
+                  g[c][y] = (x < W && y < H) ? g[c][y] - shift : 0.f;
+                  part += g[c][y];
+                }
+              }
+              Gs = group_sum_shfl<L>(part, gmask);
+            } else {
+              shift = ST(SSH0, j);
+              Gs = ST(SGS, j);
+              load_shifted<L, C, R>(a, off, W, H, lg, W == L * C && H == R, shift, g);
+            }
+          const float sx = pe[2], sy = iso ? pe[2] : pe[3];
+          const float ivx = inv_sq(sx), ivy = inv_sq(sy);
+          const float nhx = -0.5f * ivx, nhy = -0.5f * ivy;
+          float ex[C], dxv[C];
+          {
+            // column profile e_x and the column moments sum dx^m e_x^n
+            float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const int x = lg + L * c;
+              const float d = (float)x - pe[0];
+              const float e = (x < W) ? __expf(d * d * nhx) : 0.f;
+              ex[c] = e;
+              dxv[c] = d;
+              const float e2 = e * e, de = d * e, de2 = d * e2;
+              m[0] += e;
+              m[1] += e2;
+              m[2] += de;
+              m[3] = fmaf(d, de, m[3]);
+              m[4] += de2;
+              m[5] = fmaf(d, de2, m[5]);
+              m[6] = fmaf(d * d, de2, m[6]);
+              m[7] = fmaf(d * d * d, de2, m[7]);
+            }
+            // slots: 1 X01, 2 X02, 5 X11, 6 X21, 7 X12, 8 X22, 9 X32, 10 X42
+            red[1 * RS + lg] = m[0];
+            red[2 * RS + lg] = m[1];
+    #pragma unroll
+            for (int k = 0; k < 6; ++k) red[(5 + k) * RS + lg] = m[2 + k];
+          }
+          {
+            // row profile e_y into the group's table, and the row moments
+            float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    #pragma unroll
+            for (int k = 0; k < NR; ++k) {
+              const int y = lg + L * k;
+              if (y < R) {
+                const float d = (float)y - pe[1];
+                const float e = (y < H) ? __expf(d * d * nhy) : 0.f;
+                tab[y] = e;
+                const float e2 = e * e, de = d * e, de2 = d * e2;
+                m[0] += e;
+                m[1] += e2;
+                m[2] += de;
+                m[3] = fmaf(d, de, m[3]);
+                m[4] += de2;
+                m[5] = fmaf(d, de2, m[5]);
+                m[6] = fmaf(d * d, de2, m[6]);
+                m[7] = fmaf(d * d * d, de2, m[7]);
+              }
+            }
+            // slots: 3 Y01, 4 Y02, 11 Y11, 12 Y21, 13 Y12, 14 Y22, 15 Y32, 16 Y42
+            red[3 * RS + lg] = m[0];
+            red[4 * RS + lg] = m[1];
+    #pragma unroll
+            for (int k = 0; k < 6; ++k) red[(11 + k) * RS + lg] = m[2 + k];
+          }
+          __syncwarp(gmask);
+          // pass 1: s(x) = sum_y e_y g'(x, y);  FG' partial = sum_x e_x s(x)
+          {
+            float s0[C];
+    #pragma unroll
+            for (int c = 0; c < C; ++c) s0[c] = 0.f;
+    #pragma unroll
+            for (int y = 0; y < R; ++y) {
+              const float e = tab[y];
+    #pragma unroll
+              for (int c = 0; c < C; ++c) s0[c] = fmaf(e, g[c][y], s0[c]);
+            }
+            float fg = 0.f;
+    #pragma unroll
+            for (int c = 0; c < C; ++c) fg = fmaf(ex[c], s0[c], fg);
+            red[lg] = fg;
+          }
+          group_reduce<L, K1>(red, tot1, lg, gmask);
+          const float4 t1a = reinterpret_cast<const float4 *>(tot1)[0];
+          const float FG = t1a.x, X01 = t1a.y, X02 = t1a.z, Y01 = t1a.w, Y02 = tot1[4];
+          const float F = X01 * Y01, FF = X02 * Y02;
+          const float D = fmaf(Nf, FF, -F * F);
+          const bool okD = D > 0.f && isfinite(D);
+          const float iD = __fdividef(1.f, D);
+          const float alpha = (Nf * FG - F * Gs) * iD;  // Eq. 6
+          float bp = (Gs * FF - F * FG) * iD;           // beta^ - shift
+          if (first_eval && okD) {
+            // move the shift to the integer nearest beta^ (exact for integer pixel values)
+            const float dl0 = rintf(bp);
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const int x = lg + L * c;
+    #pragma unroll
+              for (int y = 0; y < R; ++y) g[c][y] = (x < W && y < H) ? g[c][y] - dl0 : 0.f;
+            }
+            Gs = fmaf(-Nf, dl0, Gs);
+            shift += dl0;
+            bp -= dl0;
+          }
+          // pass 2: u = g' - alpha e_x e_y; chi_u = sum u^2; row-weighted sums of e_y u
+          {
+            float ca[C], ch0[C], ch1[C], t0[C], t1[C], t2[C];
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+              ca[c] = -alpha * ex[c];
+              ch0[c] = ch1[c] = t0[c] = t1[c] = t2[c] = 0.f;
+            }
+    #pragma unroll
+            for (int y = 0; y < R; ++y) {
+              const float e = tab[y];
+              const float yy = (float)y - yc0;
+    #pragma unroll
+              for (int c = 0; c < C; ++c) {
+                const float u = fmaf(ca[c], e, g[c][y]);
+                if (y & 1) ch1[c] = fmaf(u, u, ch1[c]);
+                else ch0[c] = fmaf(u, u, ch0[c]);
+                const float w = e * u;
+                t0[c] += w;
+                t1[c] = fmaf(yy, w, t1[c]);
+                t2[c] = fmaf(yy * yy, w, t2[c]);
+              }
+            }
+            float v2[K2] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const float e = ex[c], d = dxv[c];
+              const float et0 = e * t0[c];
+              v2[0] += ch0[c] + ch1[c];
+              v2[1] += et0;
+              v2[2] = fmaf(d, et0, v2[2]);
+              v2[3] = fmaf(d * d, et0, v2[3]);
+              v2[4] = fmaf(e, t1[c], v2[4]);
+              v2[5] = fmaf(e, t2[c], v2[5]);
+            }
+    #pragma unroll
+            for (int k = 0; k < K2; ++k) red[k * RS + lg] = v2[k];
+          }
+          group_reduce<L, K2>(red, tot2, lg, gmask);
+          const float chiu = tot2[0];
+          const float Su = fmaf(-alpha, F, Gs);             // sum u = G' - alpha F
+          float chi = chiu - 2.f * bp * Su + Nf * bp * bp;  // Eq. 2: sum (u - beta')^2
+          if (!okD || !isfinite(alpha)) chi = __int_as_float(0x7fc00000);
+
+          // -------------------------------------------------------------- chi^2 change
+          // delta = chi_t^2 - chi_b^2, refined near the two decision thresholds. The window
+          // covers the FP32 error of each chi^2: rounding alpha f and the profile in every
+          // residual u gives errors of ~eps |alpha| f per pixel, i.e. a chi^2 error of about
+          // 6 eps |alpha| sqrt(chi^2 F(bold) / N); the window takes four times that per point.
+          const float chib = ST(SCHIB, j), noiseb = ST(SNOISEB, j);
+          const float noise =
+              24.f * 5.9604645e-8f * fabsf(alpha) * sqrtf(fmaxf(chi, 0.f) * FF * __fdividef(1.f, Nf));
+          float delta = chi - chib;
+          const float win = kTieWindow * chib + noise + noiseb;
+          if (!first_eval && isfinite(chi) && isfinite(chib) && delta >= -a.min_delta * chib - win &&
+              delta <= win) {
+            float p[4];
+  #pragma unroll
+            for (int k = 0; k < 4; ++k) p[k] = ST(SP + k, j);
+            const float alb = ST(SALB, j), bpb = ST(SBPB, j);
+            const float sbx = p[2], sby = iso ? p[2] : p[3];
+            const float ivbx = inv_sq(sbx), ivby = inv_sq(sby);
+            const float nhbx = -0.5f * ivbx, nhby = -0.5f * ivby;
+            const float dsx = sx - sbx, dsy = sy - sby;
+            const float d0 = pe[0] - p[0], d1 = pe[1] - p[1];
+            const float kx = dsx * (sx + sbx) * ivx * ivbx, ky = dsy * (sy + sby) * ivy * ivby;
+            float mx[C], omx[C], exb[C], cab[C];
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const int x = lg + L * c;
+              const float db = (float)x - p[0], dt = dxv[c];
+              // exponent difference x_t - x_b, from the parameter differences
+              const float dxe = 0.5f * fmaf(d0 * (dt + db), ivx, db * db * kx);
+              mx[c] = (x < W) ? expm1_small(dxe) : 0.f;
+              omx[c] = 1.f + mx[c];
+              exb[c] = (x < W) ? __expf(db * db * nhbx) : 0.f;
+              cab[c] = -alb * exb[c];
+            }
+    #pragma unroll
+            for (int k = 0; k < NR; ++k) {
+              const int y = lg + L * k;
+              if (y < R) {
+                const float db = (float)y - p[1], dt = (float)y - pe[1];
+                const float dye = 0.5f * fmaf(d1 * (dt + db), ivy, db * db * ky);
+                rtab[y] = (y < H) ? make_float2(expm1_small(dye), __expf(db * db * nhby))
+                                  : make_float2(0.f, 0.f);
+              }
+            }
+            __syncwarp(gmask);
+            const float dal = alpha - alb, dbp = bp - bpb;
+            float acc = 0.f;
+    #pragma unroll
+            for (int y = 0; y < R; ++y) {
+              if (y < H) {  // padding rows and columns are not part of the spot
+                const float2 q = rtab[y];  // (e_y,t / e_y,b - 1, e_y,b)
+    #pragma unroll
+                for (int c = 0; c < C; ++c) {
+                  if (lg + L * c < W) {
+                    const float fb = exb[c] * q.y;
+                    const float tt = fmaf(q.x, omx[c], mx[c]);             // f_t / f_b - 1
+                    const float dh = fmaf(fb, fmaf(alpha, tt, dal), dbp);  // h_t - h_b
+                    const float rb = fmaf(cab[c], q.y, g[c][y]) - bpb;     // g - h_b
+                    acc = fmaf(dh, fmaf(-2.f, rb, dh), acc);
+                  }
+                }
+              }
+            }
+            red[lg] = acc;
+            group_reduce<L, 1>(red, tot3, lg, gmask);
+            delta = tot3[0];
+          }
+
+            // hand the results to the slot's lane
+            if (lg < 5) {
+              const float v = lg == 0 ? alpha : lg == 1 ? bp : lg == 2 ? chi : lg == 3 ? noise : delta;
+              RES(lg, j) = v;
+            }
+  #pragma unroll
+            for (int k0 = 0; k0 < K1; k0 += L)
+              if (k0 + lg < K1) RES(RT1 + k0 + lg, j) = tot1[k0 + lg];
+            if (lg < K2) RES(RT2 + lg, j) = tot2[lg];
+            if (first_eval && lg == 0) {
+              ST(SSH0, j) = shift;
+              ST(SGS, j) = Gs;
             }
           }
           __syncwarp();
-          const float dal = alpha - alb, dbp = bp - bpb;
-          float acc = 0.f;
-#pragma unroll
-          for (int y = 0; y < R; ++y) {
-            if (y < H && x < W) {
-              const float2 q = rtab[y];
-              const float fb = exb * q.y;
-              const float tt = fmaf(q.x, omx, mx);
-              const float dh = fmaf(fb, fmaf(alpha, tt, dal), dbp);
-              const float rb = fmaf(cab, q.y, g[y]) - bpb;
-              acc = fmaf(dh, fmaf(-2.f, rb, dh), acc);
-            }
-          }
-          red[lg] = acc;
-          group_reduce<L, 1>(red, tot3, lg, full);
-          delta = tot3[0];
         }
-        // hand the results to the slot's lane
-        if (lane < 5) {
-          const float v = lane == 0 ? alpha : lane == 1 ? bp : lane == 2 ? chi : lane == 3 ? noise : delta;
-          RES(lane, j) = v;
-        }
-        if (lane < K1) RES(RT1 + lane, j) = tot1[lane];
-        if (lane < K2) RES(RT2 + lane, j) = tot2[lane];
-        if (first_eval && lane == 0) {
-          ST(SSH0, j) = shift;
-          ST(SGS, j) = Gs;
-        }
-        __syncwarp();
       }
 
       // -------------------------------------------------------------- LM step, lane per slot
@@ -1395,20 +1691,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel_batched(FitArg
 // id -> (L, C, R); one kernel instantiation each. For every row bound R, the width
 // bound 8 has (4,2) (8,1); 16 has (4,4) (8,2) (16,1); 24 has (8,3); 32 has (8,4) (16,2)
 // (32,1).
-// L = 1 marks the batched kernel (one lane per spot for the LM step, 32 columns per pass),
-// ids 36..39 for R = 8, 16, 24, 32.
+// Per-spot configurations 0..35 (L, C, R), then batched ones (same geometry per evaluation,
+// one lane per spot for the LM step): for every row bound, width bound 32 has (32, 1) and
+// (16, 2); 24 has (8, 3); 16 has (16, 1); 8 has (8, 1).
 struct CfgDesc {
-  int L, C, R;
+  int L, C, R, batched;
 };
 #define FS_CONFIGS_R(X, b, R)                                                                 \
   X(b + 0, 4, 2, R) X(b + 1, 8, 1, R) X(b + 2, 4, 4, R) X(b + 3, 8, 2, R) X(b + 4, 16, 1, R) \
   X(b + 5, 8, 3, R) X(b + 6, 8, 4, R) X(b + 7, 16, 2, R) X(b + 8, 32, 1, R)
 #define FS_CONFIGS(X) \
   FS_CONFIGS_R(X, 0, 8) FS_CONFIGS_R(X, 9, 16) FS_CONFIGS_R(X, 18, 24) FS_CONFIGS_R(X, 27, 32)
-#define FS_BATCHED(X) X(36, 8) X(37, 16) X(38, 24) X(39, 32)
+#define FS_BATCHED_R(X, R) X(32, 1, R) X(16, 2, R) X(8, 3, R) X(16, 1, R) X(8, 1, R)
+#define FS_BATCHED(X) FS_BATCHED_R(X, 8) FS_BATCHED_R(X, 16) FS_BATCHED_R(X, 24) FS_BATCHED_R(X, 32)
 
-#define FS_DESC(id, L, C, R) {L, C, R},
-#define FS_BDESC(id, R) {1, 32, R},
+#define FS_DESC(id, L, C, R) {L, C, R, 0},
+#define FS_BDESC(L, C, R) {L, C, R, 1},
 constexpr CfgDesc kConfigs[] = {FS_CONFIGS(FS_DESC) FS_BATCHED(FS_BDESC)};
 #undef FS_DESC
 #undef FS_BDESC
@@ -1416,15 +1714,15 @@ constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 typedef void (*FitKernelFn)(FitArgs, ClassList);
 #define FS_PTR(id, L, C, R) &fit_kernel<L, C, R>,
-#define FS_BPTR(id, R) &fit_kernel_batched<R>,
+#define FS_BPTR(L, C, R) &fit_kernel_batched<L, C, R>,
 const FitKernelFn kKernels[] = {FS_CONFIGS(FS_PTR) FS_BATCHED(FS_BPTR)};
 #undef FS_PTR
 #undef FS_BPTR
 static_assert(sizeof(kKernels) / sizeof(kKernels[0]) == kNumConfigs, "one kernel per configuration");
 
 size_t config_smem_bytes(int cfg) {
-  const int R = kConfigs[cfg].R;
-  const int per_warp = kConfigs[cfg].L == 1 ? batched_warp_floats(R) : warp_smem_floats(kConfigs[cfg].L, R);
+  const CfgDesc &c = kConfigs[cfg];
+  const int per_warp = c.batched ? batched_warp_floats(c.L, c.R) : warp_smem_floats(c.L, c.R);
   return (size_t)kWarpsPerBlock * per_warp * sizeof(float);
 }
 
@@ -1491,9 +1789,11 @@ std::once_flag g_init_once;
 std::mutex g_cfg_mutex;
 thread_local int g_last_cuda_error = 0;
 
-int config_for(int L, int C, int R) {
+int config_for(int L, int C, int R, int batched) {
   for (int i = 0; i < kNumConfigs; ++i)
-    if (kConfigs[i].L == L && kConfigs[i].C == C && kConfigs[i].R == R) return i;
+    if (kConfigs[i].L == L && kConfigs[i].C == C && kConfigs[i].R == R &&
+        kConfigs[i].batched == batched)
+      return i;
   return -1;
 }
 
@@ -1506,13 +1806,22 @@ bool config_fits(int cfg, int cls) {
   return cols >= wmax && cols < wmax + 8 && kConfigs[cfg].R == hmax;
 }
 
+// Built-in choice per size class (lanes, cols, batched), from timing every usable
+// configuration on 131,072-spot samples at each class's bound size on a GB300: the batched
+// kernel wins everywhere except 24 x 16 and 24 x 32 (3 columns per lane at 16+ rows
+// leave too few resident warps).
+constexpr int kDefaultCfg[kNumClasses][3] = {
+    {8, 1, 1},  {8, 1, 1},  {8, 1, 1},  {8, 1, 1},    // width bound 8, rows 8..32
+    {16, 1, 1}, {16, 1, 1}, {16, 1, 1}, {16, 1, 1},   // 16
+    {8, 3, 1},  {8, 3, 0},  {8, 3, 1},  {8, 3, 0},    // 24
+    {16, 2, 1}, {32, 1, 1}, {32, 1, 1}, {32, 1, 1}};  // 32
+
+int default_config(int cls) {
+  return config_for(kDefaultCfg[cls][0], kDefaultCfg[cls][1], (cls % 4 + 1) * 8, kDefaultCfg[cls][2]);
+}
+
 void init_defaults() {
-  // by width bound 8..32; (1, 32) is the batched kernel
-  static const int lc[4][2] = {{8, 1}, {16, 1}, {8, 3}, {1, 32}};
-  for (int cls = 0; cls < kNumClasses; ++cls) {
-    const int wb = cls / 4, hb = cls % 4;
-    g_class_cfg[cls] = (int8_t)config_for(lc[wb][0], lc[wb][1], (hb + 1) * 8);
-  }
+  for (int cls = 0; cls < kNumClasses; ++cls) g_class_cfg[cls] = (int8_t)default_config(cls);
 }
 
 struct ClassTable {
@@ -1686,6 +1995,16 @@ int fit_spots_config_info(int config, int *lanes, int *cols, int *rows) {
   if (cols) *cols = kConfigs[config].C;
   if (rows) *rows = kConfigs[config].R;
   return FS_OK;
+}
+
+int fit_spots_default_config(int size_class) {
+  if (size_class < 0 || size_class >= kNumClasses) return FS_ERR_ARG;
+  return default_config(size_class);
+}
+
+int fit_spots_config_batched(int config) {
+  if (config < 0 || config >= kNumConfigs) return FS_ERR_ARG;
+  return kConfigs[config].batched;
 }
 
 int fit_spots_config_fits(int size_class, int config) {

@@ -43,6 +43,10 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_uniform.restype = i
         lib.fit_spots_uniform_workspace.argtypes = []
         lib.fit_spots_uniform_workspace.restype = sz
+        lib.fit_spots_default_config.argtypes = [i]
+        lib.fit_spots_default_config.restype = i
+        lib.fit_spots_config_batched.argtypes = [i]
+        lib.fit_spots_config_batched.restype = i
         lib.fit_spots_config_fits.argtypes = [i, i]
         lib.fit_spots_config_fits.restype = i
         lib.fit_spots_backward.argtypes = [vp, i, i64, vp, vp, vp, i64, vp, vp, vp, vp,
@@ -189,19 +193,29 @@ def fit_batch(batch, **kw) -> dict:
     return fit(batch.images, batch.offsets, batch.dims, batch.init, batch.model, **kw)
 
 
-def configs() -> list[tuple[int, int, int]]:
+def configs() -> list[tuple[int, int, int, int]]:
+    """(lanes, cols, rows, batched) of every compiled configuration, by id."""
     lib = library()
     out = []
     for c in range(lib.fit_spots_num_configs()):
         L, C, R = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(lib.fit_spots_config_info(c, ctypes.byref(L), ctypes.byref(C), ctypes.byref(R)),
               "fit_spots_config_info")
-        out.append((L.value, C.value, R.value))
+        b = lib.fit_spots_config_batched(c)
+        check(min(b, 0), "fit_spots_config_batched")
+        out.append((L.value, C.value, R.value, b))
     return out
 
 
 def get_config(size_class: int) -> int:
     return int(library().fit_spots_get_config(int(size_class)))
+
+
+def default_config(size_class: int) -> int:
+    """The library's built-in configuration for a size class."""
+    c = int(library().fit_spots_default_config(int(size_class)))
+    check(min(c, 0), "fit_spots_default_config")
+    return c
 
 
 def config_fits(size_class: int, config: int) -> bool:

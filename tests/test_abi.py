@@ -93,15 +93,15 @@ def test_size_classes_and_configs(lib):
     from paper_2106_02045_gb300 import fitspots
     assert lib.fit_spots_num_classes() == 16
     cfgs = fitspots.configs()
-    assert len(cfgs) == lib.fit_spots_num_configs() == 40
+    assert len(cfgs) == lib.fit_spots_num_configs() == 56
+    assert sum(c[3] for c in cfgs) == 20 and lib.fit_spots_config_batched(99) == -8
     for cls in range(16):
         wmax, hmax = (cls // 4 + 1) * 8, (cls % 4 + 1) * 8
         usable = [c for c in range(len(cfgs)) if fitspots.config_fits(cls, c)]
         assert usable, cls
         for c in usable:
-            L, C, R = cfgs[c]
+            L, C, R, batched = cfgs[c]
             assert L * C >= wmax and L * C < wmax + 8 and R == hmax and 32 % L == 0
-            assert L > 1 or (C == 32 and wmax == 32)   # batched kernel: 32 columns
         assert fitspots.get_config(cls) in usable
     assert lib.fit_spots_set_config(15, 0) == -8          # (4,2,8) cannot hold 32x32
     keep = fitspots.get_config(15)

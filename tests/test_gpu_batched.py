@@ -35,7 +35,7 @@ def _use(kind):
     cfgs = fitspots.configs()
     for cls in WIDE:
         R = (cls % 4 + 1) * 8
-        fitspots.set_config(cls, cfgs.index((32, 1, R) if kind == "per_spot" else (1, 32, R)))
+        fitspots.set_config(cls, cfgs.index((32, 1, R, 0) if kind == "per_spot" else (32, 1, R, 1)))
 
 
 def _both(run):

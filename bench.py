@@ -43,6 +43,7 @@ SMS, LANES_PER_SM = 152, 128
 CONVERGED = (1, 2, 3, 4)
 PROFILE = ROOT / "profiles" / "fit_kernel_ell32.md"
 SOURCE = ROOT / "paper_2106_02045_gb300" / "csrc" / "fitspots.cu"
+E2E_CHUNK = 125_000   # spots per chunk of the host-buffer call (8 chunks per 1,000,000)
 BWD_SOURCE = ROOT / "paper_2106_02045_gb300" / "csrc" / "backward.cu"
 BWD_PROFILE = ROOT / "profiles" / "backward_iso16.md"
 
@@ -462,26 +463,25 @@ def _extra_serving(args, dev) -> dict:
 
 
 def _e2e(args, b, out, ws, stream, barrier, world, dev):
-    """The metric through the public API from pinned host buffers, copies included."""
+    """The metric through the public host-buffer call (fit_spots_uniform_host): pinned host
+    images and start values in, host results out, copies overlapped with the fits chunk by
+    chunk, all inside the timed region."""
     import numpy as np
     import torch
-    import torch.distributed as dist
     from paper_2106_02045_gb300 import fitspots, synth
     h_img = torch.empty(b.images.shape, dtype=b.images.dtype, pin_memory=True)
     h_img.copy_(b.images)
     h_init = torch.empty(b.init.shape, dtype=b.init.dtype, pin_memory=True)
     h_init.copy_(b.init)
-    h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
-    d_img = torch.empty_like(b.images)
-    d_init = torch.empty_like(b.init)
+    h_out = fitspots.alloc_host_outputs(b.n)
+    chunk = E2E_CHUNK
+    dtype = fitspots.U16 if b.images.dtype == torch.uint16 else fitspots.F32
+    d_ws = torch.empty(fitspots.host_workspace_bytes(min(chunk, b.n), W, H, dtype),
+                       dtype=torch.uint8, device=dev)
 
     def e2e_step():
-        d_img.copy_(h_img, non_blocking=True)
-        d_init.copy_(h_init, non_blocking=True)
-        fitspots.fit_uniform(d_img, W, H, synth.MODEL_ELLIPTIC, d_init, out=out, workspace=ws,
-                             stream=stream)
-        for k in out:
-            h_out[k].copy_(out[k], non_blocking=True)
+        fitspots.fit_uniform_host(h_img, W, H, synth.MODEL_ELLIPTIC, h_init, chunk=chunk,
+                                  out=h_out, workspace=d_ws, device=dev, stream=stream)
 
     e2e_steps = max(1, min(args.steps, 5))
     e2e_step()
@@ -499,7 +499,8 @@ def _e2e(args, b, out, ws, stream, barrier, world, dev):
     ms_max, conv_sum = job_totals(e2e_ms, conv_e2e, world, dev)
     e2e_value = conv_sum / (ms_max * 1e-3)
 
-    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "chunk_spots": chunk, "call": "fit_spots_uniform_host (copies overlapped with fits)"}
 
 
 def main() -> None:

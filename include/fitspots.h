@@ -124,6 +124,32 @@ int fit_spots_uniform(const void *images, int dtype, int width, int height, int 
                       int32_t *out_evals, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * fit_spots_uniform from and to HOST memory, with the transfers overlapped: the batch is cut
+ * into chunks of `chunk` spots; while chunk k is fitted on `stream`, chunk k+1's pixels and
+ * start values go to the device and chunk k-1's results come back, on a copy stream the
+ * library keeps per device. Host buffers should be pinned (cudaHostAlloc / page-locked):
+ * from pageable memory the copies still work but do not overlap the fits.
+ *   images, init_params   host arrays laid out as for fit_spots_uniform
+ *   out_*                 host arrays (out_evals may be NULL)
+ *   chunk                 spots per chunk, >= 1 (FS_ERR_ARG otherwise); larger chunks keep
+ *                         more of the GPU busy, smaller ones start the first fit sooner
+ *   workspace             device scratch of at least
+ *                         fit_spots_uniform_host_workspace(chunk, width, height, dtype)
+ *                         bytes, 256-byte aligned: two chunk buffers (images, start
+ *                         values, outputs, schedule header)
+ * Returns once everything is enqueued; when `stream` has completed, the host outputs hold
+ * the results, identical to those of fit_spots_uniform on the same inputs. Calls from
+ * several host threads on one device are serialised while they enqueue.
+ */
+size_t fit_spots_uniform_host_workspace(int64_t chunk, int width, int height, int dtype);
+int fit_spots_uniform_host(const void *images, int dtype, int width, int height, int model_id,
+                           const float *init_params, int64_t n, int max_iter, double max_error,
+                           double min_delta, double min_step, float *out_params,
+                           float *out_alpha, float *out_beta, float *out_chi2,
+                           int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                           int64_t chunk, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * fit_spots without a caller-provided workspace, for callers that cannot allocate device
  * memory: code that runs where cudaMalloc is unavailable or forbidden (inside a region
  * being captured into a CUDA graph, a real-time loop with a no-allocation rule, a plugin

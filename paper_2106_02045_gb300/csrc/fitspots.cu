@@ -44,6 +44,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "fitspots.h"
@@ -1957,6 +1958,68 @@ int static_workspace(void **ptr) {
   return FS_OK;
 }
 
+// ------------------------------------------------------------------ host-buffer pipeline
+// One chunk buffer in the device workspace of fit_spots_uniform_host: images, start values,
+// the seven outputs and the schedule header, each 256-byte aligned.
+struct ChunkLayout {
+  size_t images, init, params, alpha, beta, chi2, state, iters, evals, sched, bytes;
+};
+
+ChunkLayout chunk_layout(int64_t chunk, int width, int height, int dtype) {
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t esz = dtype == FS_U16 ? 2 : 4, c = (size_t)chunk;
+  ChunkLayout l;
+  size_t o = 0;
+  l.images = o; o += up(c * width * height * esz);
+  l.init = o; o += up(c * 16);
+  l.params = o; o += up(c * 16);
+  l.alpha = o; o += up(c * 4);
+  l.beta = o; o += up(c * 4);
+  l.chi2 = o; o += up(c * 4);
+  l.state = o; o += up(c * 4);
+  l.iters = o; o += up(c * 4);
+  l.evals = o; o += up(c * 4);
+  l.sched = o; o += up(kSchedHeaderBytes);
+  l.bytes = o;
+  return l;
+}
+
+// Per device: the copy stream and the events that order the two chunk buffers.
+struct HostPipe {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t in_ready[2] = {nullptr, nullptr};   // chunk's inputs on the device
+  cudaEvent_t fitted[2] = {nullptr, nullptr};     // chunk's fit done
+  cudaEvent_t drained = nullptr;                  // last results copied back
+  std::mutex mu;
+};
+HostPipe g_pipe[64];
+
+int host_pipe(HostPipe **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return FS_ERR_ARG;
+  HostPipe &p = g_pipe[dev];
+  if (!p.copy) {
+    std::lock_guard<std::mutex> lk(p.mu);
+    if (!p.copy) {
+      cudaStream_t s = nullptr;
+      if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+        return set_cuda_error(e);
+      for (int b = 0; b < 2; ++b) {
+        if ((e = cudaEventCreateWithFlags(&p.in_ready[b], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p.fitted[b], cudaEventDisableTiming)) != cudaSuccess)
+          return set_cuda_error(e);
+      }
+      if ((e = cudaEventCreateWithFlags(&p.drained, cudaEventDisableTiming)) != cudaSuccess)
+        return set_cuda_error(e);
+      p.copy = s;
+    }
+  }
+  *out = &p;
+  return FS_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -2120,6 +2183,96 @@ int fit_spots_uniform(const void *images, int dtype, int width, int height, int 
   kKernels[cfg]<<<grid, kWarpsPerBlock * 32, config_smem_bytes(cfg), st>>>(a, cl);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_cuda_error(e);
+  return FS_OK;
+}
+
+size_t fit_spots_uniform_host_workspace(int64_t chunk, int width, int height, int dtype) {
+  if (chunk < 1 || width < 1 || height < 1 || width > kMaxSide || height > kMaxSide ||
+      (dtype != FS_U16 && dtype != FS_F32))
+    return 0;
+  return 2 * chunk_layout(chunk, width, height, dtype).bytes;
+}
+
+int fit_spots_uniform_host(const void *images, int dtype, int width, int height, int model_id,
+                           const float *init_params, int64_t n, int max_iter, double max_error,
+                           double min_delta, double min_step, float *out_params,
+                           float *out_alpha, float *out_beta, float *out_chi2,
+                           int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                           int64_t chunk, void *workspace, size_t ws_bytes, void *stream) {
+  int rc = check_common(dtype, n, max_iter, max_error, min_delta, min_step);
+  if (rc) return rc;
+  const int P = model_id == FS_MODEL_ISO ? 3 : 4;
+  if ((model_id != FS_MODEL_ISO && model_id != FS_MODEL_ELLIPTIC) || width < 3 || height < 3 ||
+      width > kMaxSide || height > kMaxSide || width * height <= P + 2 || chunk < 1 ||
+      chunk > INT32_MAX)
+    return FS_ERR_ARG;
+  if (n == 0) return FS_OK;
+  if (!images || !init_params || !out_params || !out_alpha || !out_beta || !out_chi2 ||
+      !out_state || !out_iters || !workspace)
+    return FS_ERR_NULL;
+  if (chunk > n) chunk = n;
+  const ChunkLayout l = chunk_layout(chunk, width, height, dtype);
+  if (ws_bytes < 2 * l.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return FS_ERR_WORKSPACE;
+  HostPipe *pp = nullptr;
+  if ((rc = host_pipe(&pp))) return rc;
+  std::lock_guard<std::mutex> lk(pp->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream), cp = pp->copy;
+  const size_t esz = dtype == FS_U16 ? 2 : 4, px = (size_t)width * height;
+  const int64_t nchunks = (n + chunk - 1) / chunk;
+  char *ws = static_cast<char *>(workspace);
+  cudaError_t e = cudaSuccess;
+  // the copy stream starts after whatever the caller queued on `stream` before this call
+  if ((e = cudaEventRecord(pp->drained, st)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(cp, pp->drained, 0)) != cudaSuccess)
+    return set_cuda_error(e);
+  auto upload = [&](int64_t k) -> cudaError_t {
+    char *b = ws + (k & 1) * l.bytes;
+    const int64_t s0 = k * chunk, m = std::min<int64_t>(chunk, n - s0);
+    cudaError_t x = cudaMemcpyAsync(b + l.images, static_cast<const char *>(images) + s0 * px * esz,
+                                    m * px * esz, cudaMemcpyHostToDevice, cp);
+    if (x == cudaSuccess)
+      x = cudaMemcpyAsync(b + l.init, init_params + 4 * s0, m * 16, cudaMemcpyHostToDevice, cp);
+    if (x == cudaSuccess) x = cudaEventRecord(pp->in_ready[k & 1], cp);
+    return x;
+  };
+  if ((e = upload(0)) != cudaSuccess) return set_cuda_error(e);
+  for (int64_t k = 0; k < nchunks; ++k) {
+    // chunk k+1 goes up while chunk k is fitted (its buffer was drained, in copy-stream
+    // order, by chunk k-1's download)
+    if (k + 1 < nchunks && (e = upload(k + 1)) != cudaSuccess) return set_cuda_error(e);
+    char *b = ws + (k & 1) * l.bytes;
+    const int64_t s0 = k * chunk, m = std::min<int64_t>(chunk, n - s0);
+    if ((e = cudaStreamWaitEvent(st, pp->in_ready[k & 1], 0)) != cudaSuccess)
+      return set_cuda_error(e);
+    rc = fit_spots_uniform(b + l.images, dtype, width, height, model_id,
+                           reinterpret_cast<const float *>(b + l.init), m, max_iter, max_error,
+                           min_delta, min_step, reinterpret_cast<float *>(b + l.params),
+                           reinterpret_cast<float *>(b + l.alpha),
+                           reinterpret_cast<float *>(b + l.beta),
+                           reinterpret_cast<float *>(b + l.chi2),
+                           reinterpret_cast<int32_t *>(b + l.state),
+                           reinterpret_cast<int32_t *>(b + l.iters),
+                           out_evals ? reinterpret_cast<int32_t *>(b + l.evals) : nullptr,
+                           b + l.sched, kSchedHeaderBytes, stream);
+    if (rc) return rc;
+    if ((e = cudaEventRecord(pp->fitted[k & 1], st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(cp, pp->fitted[k & 1], 0)) != cudaSuccess)
+      return set_cuda_error(e);
+    struct { void *dst; size_t off, sz; } outs[7] = {
+        {out_params + 4 * s0, l.params, 16}, {out_alpha + s0, l.alpha, 4},
+        {out_beta + s0, l.beta, 4},          {out_chi2 + s0, l.chi2, 4},
+        {out_state + s0, l.state, 4},        {out_iters + s0, l.iters, 4},
+        {out_evals ? out_evals + s0 : nullptr, l.evals, 4}};
+    for (auto &o : outs)
+      if (o.dst && (e = cudaMemcpyAsync(o.dst, b + o.off, m * o.sz, cudaMemcpyDeviceToHost, cp)) !=
+                       cudaSuccess)
+        return set_cuda_error(e);
+  }
+  // `stream` completes only after the last results are on the host
+  if ((e = cudaEventRecord(pp->drained, cp)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st, pp->drained, 0)) != cudaSuccess)
+    return set_cuda_error(e);
   return FS_OK;
 }
 

@@ -41,6 +41,11 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_uniform.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
                                           vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fit_spots_uniform.restype = i
+        lib.fit_spots_uniform_host.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
+                                               vp, vp, vp, vp, vp, vp, vp, i64, vp, sz, vp]
+        lib.fit_spots_uniform_host.restype = i
+        lib.fit_spots_uniform_host_workspace.argtypes = [i64, i, i, i]
+        lib.fit_spots_uniform_host_workspace.restype = sz
         lib.fit_spots_uniform_workspace.argtypes = []
         lib.fit_spots_uniform_workspace.restype = sz
         lib.fit_spots_default_config.argtypes = [i]
@@ -185,6 +190,60 @@ def fit_uniform(images: torch.Tensor, width: int, height: int, model: int, init:
             _ptr(o["iters"]), _ptr(o.get("evals")), _ptr(workspace), workspace.numel(),
             ctypes.c_void_p(s.cuda_stream))
     check(rc, "fit_spots_uniform")
+    return o
+
+
+def alloc_host_outputs(n: int) -> dict:
+    """Pinned host buffers for the outputs of ``fit_uniform_host``."""
+    return {k: torch.empty(v, dtype=t, pin_memory=True) for k, (v, t) in dict(
+        params=((n, 4), torch.float32), alpha=(n, torch.float32), beta=(n, torch.float32),
+        chi2=(n, torch.float32), state=(n, torch.int32), iters=(n, torch.int32),
+        evals=(n, torch.int32)).items()}
+
+
+def host_workspace_bytes(chunk: int, width: int, height: int, dtype: int) -> int:
+    return int(library().fit_spots_uniform_host_workspace(int(chunk), int(width), int(height),
+                                                          int(dtype)))
+
+
+def fit_uniform_host(images: torch.Tensor, width: int, height: int, model: int,
+                     init: torch.Tensor, *, chunk: int = 131072, max_iter: int = 20,
+                     max_error: float = 0.0, min_delta: float = 1e-6, min_step: float = 1e-4,
+                     out: dict | None = None, workspace: torch.Tensor | None = None,
+                     device=None, stream: torch.cuda.Stream | None = None) -> dict:
+    """``fit_uniform`` on HOST tensors (pinned for overlap): chunks of ``chunk`` spots are
+    copied up, fitted and copied back with the copies overlapping the fits. Returns (or
+    fills ``out``) host tensors, valid once ``stream`` has completed."""
+    if images.device.type != "cpu" or init.device.type != "cpu":
+        raise FitSpotsError("images and init must be host (CPU) tensors")
+    if images.dtype == torch.uint16:
+        dtype = U16
+    elif images.dtype == torch.float32:
+        dtype = F32
+    else:
+        raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
+    if init.dtype != torch.float32 or not init.is_contiguous() or not images.is_contiguous():
+        raise FitSpotsError("images and init must be contiguous; init float32")
+    n = init.numel() // 4
+    if init.numel() != 4 * n or images.numel() < n * width * height:
+        raise FitSpotsError("init must be [n, 4] and images must hold n*W*H elements")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    o = out if out is not None else alloc_host_outputs(n)
+    for k, t in o.items():
+        if t is not None and t.device.type != "cpu":
+            raise FitSpotsError(f"out[{k!r}] must be a host tensor")
+    need = host_workspace_bytes(min(chunk, max(n, 1)), width, height, dtype)
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = library().fit_spots_uniform_host(
+            _ptr(images), dtype, int(width), int(height), int(model), _ptr(init), n,
+            int(max_iter), float(max_error), float(min_delta), float(min_step),
+            _ptr(o["params"]), _ptr(o["alpha"]), _ptr(o["beta"]), _ptr(o["chi2"]), _ptr(o["state"]),
+            _ptr(o["iters"]), _ptr(o.get("evals")), int(chunk), _ptr(workspace),
+            workspace.numel(), ctypes.c_void_p(s.cuda_stream))
+    check(rc, "fit_spots_uniform_host")
     return o
 
 

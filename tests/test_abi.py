@@ -89,6 +89,32 @@ def test_uniform_argument_checks(lib):
     assert call(max_iter=0) == -4
 
 
+def test_host_call_argument_checks(lib):
+    """fit_spots_uniform_host: sizes of its double-buffered device scratch, and the checks
+    that run before any CUDA call."""
+    one = lib.fit_spots_uniform_host_workspace(1000, 32, 32, 0)
+    # per chunk buffer: images, start values, 7 outputs, schedule header; 256-byte aligned
+    up = lambda v: (v + 255) // 256 * 256
+    assert one == 2 * (up(1000 * 32 * 32 * 2) + 2 * up(16000) + 5 * up(4000) + up(4000) + 256)
+    assert lib.fit_spots_uniform_host_workspace(1000, 32, 32, 1) > one
+    assert lib.fit_spots_uniform_host_workspace(0, 32, 32, 0) == 0
+    assert lib.fit_spots_uniform_host_workspace(10, 33, 32, 0) == 0
+    assert lib.fit_spots_uniform_host_workspace(10, 32, 32, 5) == 0
+    fake = ctypes.c_void_p(0x1000)
+
+    def call(W=32, H=32, model=1, n=10, chunk=4, ws=ctypes.c_void_p(0x10000), ws_bytes=1 << 30,
+             images=fake, max_iter=20):
+        return lib.fit_spots_uniform_host(images, 0, W, H, model, fake, n, max_iter, 0.0, 1e-6,
+                                          1e-4, fake, fake, fake, fake, fake, fake, None, chunk,
+                                          ws, ws_bytes, None)
+    assert call(chunk=0) == -8 and call(W=2) == -8 and call(model=2) == -8
+    assert call(n=0) == 0
+    assert call(images=None) == -1 and call(ws=None) == -1
+    assert call(ws_bytes=1000) == -6                          # below two chunk buffers
+    assert call(ws=ctypes.c_void_p(0x10010)) == -6            # not 256-byte aligned
+    assert call(max_iter=0) == -4
+
+
 def test_size_classes_and_configs(lib):
     from paper_2106_02045_gb300 import fitspots
     assert lib.fit_spots_num_classes() == 16

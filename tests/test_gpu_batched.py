@@ -115,3 +115,22 @@ def test_batched_writes_every_spot_and_handles_degenerate_rois():
         assert (o["state"] != -99).all() and (o["iters"] >= 1).all()
         assert o["state"][3] == -1 and o["state"][5] == -1
     assert outs[0]["state"][7] == outs[1]["state"][7]
+
+
+@pytest.mark.parametrize("name,chunk", [("ell32", 7000), ("iso15", 999)])
+def test_host_call_matches_device_call(name, chunk):
+    """fit_spots_uniform_host (pinned host buffers, chunked, copies overlapped) returns the
+    device call's results bit for bit, including a partial last chunk."""
+    b = synth.make_workload(name, 30001)
+    W, H, m = int(b.dims[0, 0]), int(b.dims[0, 1]), int(b.model[0])
+    h_img = b.images.pin_memory()
+    h_init = b.init.contiguous().pin_memory()
+    ref = fitspots.fit_uniform(b.images.to(DEV), W, H, m, b.init.to(DEV))
+    out = fitspots.fit_uniform_host(h_img, W, H, m, h_init, chunk=chunk, device=DEV)
+    torch.cuda.synchronize()
+    for k in ref:
+        a = ref[k].cpu()
+        c = out[k]
+        if a.dtype == torch.float32:
+            a, c = a.view(torch.int32), c.view(torch.int32)
+        assert torch.equal(a, c), k

@@ -1984,13 +1984,16 @@ ChunkLayout chunk_layout(int64_t chunk, int width, int height, int dtype) {
   return l;
 }
 
-// Per device: the copy stream and the events that order the two chunk buffers.
+// Per device: the copy stream and the events that order the two chunk buffers, created
+// once (std::call_once) and kept for the life of the process.
 struct HostPipe {
   cudaStream_t copy = nullptr;
   cudaEvent_t in_ready[2] = {nullptr, nullptr};   // chunk's inputs on the device
   cudaEvent_t fitted[2] = {nullptr, nullptr};     // chunk's fit done
   cudaEvent_t drained = nullptr;                  // last results copied back
-  std::mutex mu;
+  cudaError_t init_error = cudaSuccess;
+  std::once_flag once;
+  std::mutex mu;                                  // one caller enqueues at a time
 };
 HostPipe g_pipe[64];
 
@@ -2000,22 +2003,16 @@ int host_pipe(HostPipe **out) {
   if (e != cudaSuccess) return set_cuda_error(e);
   if (dev < 0 || dev >= 64) return FS_ERR_ARG;
   HostPipe &p = g_pipe[dev];
-  if (!p.copy) {
-    std::lock_guard<std::mutex> lk(p.mu);
-    if (!p.copy) {
-      cudaStream_t s = nullptr;
-      if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
-        return set_cuda_error(e);
-      for (int b = 0; b < 2; ++b) {
-        if ((e = cudaEventCreateWithFlags(&p.in_ready[b], cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&p.fitted[b], cudaEventDisableTiming)) != cudaSuccess)
-          return set_cuda_error(e);
-      }
-      if ((e = cudaEventCreateWithFlags(&p.drained, cudaEventDisableTiming)) != cudaSuccess)
-        return set_cuda_error(e);
-      p.copy = s;
+  std::call_once(p.once, [&p] {
+    cudaError_t x = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && x == cudaSuccess; ++b) {
+      x = cudaEventCreateWithFlags(&p.in_ready[b], cudaEventDisableTiming);
+      if (x == cudaSuccess) x = cudaEventCreateWithFlags(&p.fitted[b], cudaEventDisableTiming);
     }
-  }
+    if (x == cudaSuccess) x = cudaEventCreateWithFlags(&p.drained, cudaEventDisableTiming);
+    p.init_error = x;
+  });
+  if (p.init_error != cudaSuccess) return set_cuda_error(p.init_error);
   *out = &p;
   return FS_OK;
 }

@@ -787,12 +787,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, Cla
 }
 
 // ------------------------------------------------------------------ batched fit loop
-// Configuration (1, 32, R): one lane per spot for the LM step, the whole warp for the pixel
-// passes of one spot at a time. A warp keeps kSlots spots in flight. Each round it evaluates
-// every active spot at its trial point, one after another (lane = column, the arithmetic and
-// the reduction order of the (32, 1, R) configuration), then lane j runs the LM step of slot
-// j from that evaluation's sums and refills the slot when its spot finishes. The scalar LM
-// work thus runs once per 16 spots instead of once per spot. Pixels are re-read from global
+// Batched configurations (L, C, R): one lane per spot for the LM step, lane groups for the
+// pixel passes. A warp keeps kSlots spots in flight. Each round its 32 / L lane groups
+// evaluate the active spots at their trial points, 32 / L at a time (each group as one spot of
+// the per-spot kernel with the same geometry), then lane j runs the LM step of slot j from
+// that evaluation's sums and refills the slot when its spot finishes. The scalar LM work thus
+// runs once per spot instead of once per lane of a group. Pixels are re-read from global
 // memory (mostly L2) at each evaluation; slot state and evaluation results live in shared
 // memory.
 constexpr int kSlots = 16;
@@ -808,11 +808,10 @@ enum : int {
   SBPB = 28,     // beta - shift at p
   SNOISEB = 29,  // chi^2 error estimate at p
   SSH0 = 30,     // integer pixel shift (corner pixel, then moved to the nearest of beta)
-  SDL0 = 31,     // (unused)
-  SGS = 32,      // sum of shifted pixels
-  SKLAM = 33, SIT = 34, SEVALS = 35, SSPOT = 36, SOFFLO = 37, SOFFHI = 38,
-  SFLAGS = 39,   // W | H << 8 | iso << 16 | first_eval << 17 | first_trial << 18 | active << 19
-  kSlotFields = 40
+  SGS = 31,      // sum of shifted pixels
+  SKLAM = 32, SIT = 33, SEVALS = 34, SSPOT = 35, SOFFLO = 36, SOFFHI = 37,
+  SFLAGS = 38,   // W | H << 8 | iso << 16 | first_eval << 17 | first_trial << 18 | active << 19
+  kSlotFields = 39
 };
 // evaluation results handed from the warp to the slot's lane
 enum : int { RALPHA = 0, RBP, RCHI, RNOISE, RDELTA, RT1, RT2 = RT1 + K1, kResFields = RT2 + K2 };

@@ -336,8 +336,9 @@ def _timed(fn, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def _extras(args, dev, which=("mixed", "backward", "serving")) -> dict:
-    """The other hot-path rows on their workloads: mixed sizes, backward, serving."""
+def _extras(args, dev, which=("mixed", "backward", "serving", "start")) -> dict:
+    """The other hot-path rows on their workloads: mixed sizes, backward, serving, start
+    values."""
     import torch
     stream = torch.cuda.current_stream(dev)
     out = {}
@@ -352,7 +353,30 @@ def _extras(args, dev, which=("mixed", "backward", "serving")) -> dict:
         out.update(_extra_backward(dev, stream, hbm))
     if "serving" in which:
         out.update(_extra_serving(args, dev))
+    if "start" in which:
+        out.update(_extra_start(dev, stream, hbm))
     return out
+
+
+def _extra_start(dev, stream, hbm) -> dict:
+    import torch
+    from paper_2106_02045_gb300 import fitspots, synth
+    # start values on the device for the 1,000,000 ell32 ROIs (uint16), both rules
+    b = synth.make_workload("ell32", None, device=dev)
+    init = torch.empty((b.n, 4), dtype=torch.float32, device=dev)
+    res = {}
+    nbytes = b.n * (32 * 32 * 2 + 16 + 12)
+    for rule, name in ((fitspots.START_CENTROID, "centroid"), (fitspots.START_PAPER, "paper")):
+        ms = _timed(lambda: fitspots.start_values(b.images, b.offsets, b.dims, rule, out=init,
+                                                  stream=stream), 5, stream)
+        res[name] = {"ms_per_step": ms, "value": b.n / (ms * 1e-3), "unit": "spots/s",
+                     "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9,
+                                  "peak": hbm, "unit": "GB/s",
+                                  "frac": nbytes / (ms * 1e-3) / 1e9 / hbm,
+                                  "bytes_per_spot": 32 * 32 * 2 + 16 + 12}}
+    del b, init
+    return {"start": {"workload": "ell32: 1,000,000 ROIs of 32x32 uint16, start values on the "
+                                  "device (fit_spots_start)", **res}}
 
 
 def _extra_mixed(args, dev, stream) -> dict:
@@ -514,8 +538,8 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
-    ap.add_argument("--extras", default="mixed,backward,serving",
-                    help="comma-separated subset of mixed,backward,serving")
+    ap.add_argument("--extras", default="mixed,backward,serving,start",
+                    help="comma-separated subset of mixed,backward,serving,start")
     ap.add_argument("--mixed-spots", type=int, default=2_000_000)
     ap.add_argument("--serving-frames", type=int, default=20000)
     ap.add_argument("--serving-warmup", type=int, default=1000)

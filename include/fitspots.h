@@ -238,6 +238,24 @@ const char *fit_spots_strerror(int code);
 int fit_spots_last_cuda_error(void);
 
 /*
+ * Start values (x0, y0, s0, s0) for the fit, estimated on the device from each ROI's pixels
+ * (the paper estimates start values from the image before fitting, Results section).
+ *   rule FS_START_CENTROID  centre = centroid of max(g - min g, 0), the ROI centre
+ *                           ((W-1)/2, (H-1)/2) if that weight is zero everywhere
+ *   rule FS_START_PAPER     centre = the pixel whose in-ROI 3x3 neighbourhood has the
+ *                           largest mean, ties to the lowest row-major index
+ *   both                    s0 = sqrt(max(M, 1) / pi), M = #{g > (max g - min g) e^(-1/2) + min g}
+ * FP32 throughout; the decisions (the threshold test and the comparison of two means
+ * S_i / c_i > S_j / c_j as S_i c_j > S_j c_i) are exact for integer-valued pixels below 2^21.
+ * images/offsets/roi_dims as for fit_spots (W, H in 1..32); out_init device float[n][4]; an
+ * invalid ROI gets four NaNs. Asynchronous on `stream`.
+ */
+#define FS_START_CENTROID 0
+#define FS_START_PAPER 1
+int fit_spots_start(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
+                    const int32_t *roi_dims, int64_t n, int rule, float *out_init, void *stream);
+
+/*
  * Size classes and their kernel configurations.
  * A spot's size class is (ceil(W/8)-1)*4 + (ceil(H/8)-1), i.e. 16 classes for W, H in
  * 3..32. Each class runs one kernel configuration: `lanes` threads per spot (4, 8, 16

@@ -41,6 +41,8 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_uniform.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
                                           vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fit_spots_uniform.restype = i
+        lib.fit_spots_start.argtypes = [vp, i, i64, vp, vp, i64, i, vp, vp]
+        lib.fit_spots_start.restype = i
         lib.fit_spots_uniform_host.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
                                                vp, vp, vp, vp, vp, vp, vp, i64, vp, sz, vp]
         lib.fit_spots_uniform_host.restype = i
@@ -244,6 +246,36 @@ def fit_uniform_host(images: torch.Tensor, width: int, height: int, model: int,
             _ptr(o["iters"]), _ptr(o.get("evals")), int(chunk), _ptr(workspace),
             workspace.numel(), ctypes.c_void_p(s.cuda_stream))
     check(rc, "fit_spots_uniform_host")
+    return o
+
+
+START_CENTROID, START_PAPER = 0, 1
+
+
+def start_values(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
+                 rule: int = START_CENTROID, *, out: torch.Tensor | None = None,
+                 stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """Start values [n, 4] (x0, y0, s0, s0) from each ROI's pixels, on the device."""
+    dev = images.device
+    if dev.type != "cuda":
+        raise FitSpotsError("images must be a CUDA tensor")
+    dtype = U16 if images.dtype == torch.uint16 else F32 if images.dtype == torch.float32 else None
+    if dtype is None:
+        raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
+    _need(images, images.dtype, "images", dev)
+    _need(offsets, torch.int64, "offsets", dev)
+    _need(dims, torch.int32, "dims", dev)
+    n = offsets.numel()
+    if dims.numel() != 2 * n:
+        raise FitSpotsError("dims must be [n, 2]")
+    o = out if out is not None else torch.empty((n, 4), dtype=torch.float32, device=dev)
+    _need(o, torch.float32, "out", dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = library().fit_spots_start(_ptr(images), dtype, images.numel(), _ptr(offsets),
+                                       _ptr(dims), n, int(rule), _ptr(o),
+                                       ctypes.c_void_p(s.cuda_stream))
+    check(rc, "fit_spots_start")
     return o
 
 

@@ -14,7 +14,8 @@
 // 2^21 (uint16 data, photon counts): a0 and the threshold are formed as fl(fl(a0 c) + b0)
 // with c = fl(e^(-1/2)); two neighbourhood means S_i / c_i and S_j / c_j are compared as
 // S_i c_j against S_j c_i, where S is the FP32 sum of the in-ROI neighbours in row-major
-// order. One warp per spot, lanes over the pixels (row-major, 32 apart).
+// order. One warp per spot, lanes over the pixels (row-major, 32 apart); the ROI is staged in
+// shared memory once and both passes and the 3 x 3 windows read it there.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -44,6 +45,8 @@ __device__ __forceinline__ float px(const T *p, int i) {
   return (float)__ldg(p + i);
 }
 
+constexpr int kStartWarpFloats = 1024;  // one ROI of at most 32 x 32 pixels per warp
+
 // candidate (mean numerator S, neighbour count c, pixel index i) of the 3 x 3 rule: does a
 // beat b? Larger S / c, ties to the lower index.
 __device__ __forceinline__ bool beats(float Sa, float ca, int ia, float Sb, float cb, int ib) {
@@ -53,6 +56,8 @@ __device__ __forceinline__ bool beats(float Sa, float ca, int ia, float Sb, floa
 
 template <typename T>
 __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
+  __shared__ float sm_all[(kStartThreads / 32) * kStartWarpFloats];
+  float *const sg = sm_all + (threadIdx.x >> 5) * kStartWarpFloats;  // the warp's ROI
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (kStartThreads / 32);
   const T *const img = static_cast<const T *>(a.images);
@@ -65,13 +70,16 @@ __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
     }
     const T *const g = img + off;
     const int N = W * H;
-    // min and max
+    // the ROI into shared memory (read once, coalesced), min and max on the way
+    __syncwarp();
     float lo = INFINITY, hi = -INFINITY;
     for (int i = lane; i < N; i += 32) {
       const float v = px(g, i);
+      sg[i] = v;
       lo = fminf(lo, v);
       hi = fmaxf(hi, v);
     }
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -88,7 +96,7 @@ __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
     const int sy = 32 / W, sx = 32 - sy * W;
     int y = lane / W, x = lane - (lane / W) * W;
     for (int i = lane; i < N; i += 32) {
-      const float v = px(g, i);
+      const float v = sg[i];
       M += v > thr;
       const float w = fmaxf(v - b0, 0.f);
       sw += w;
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
           for (int dx = -1; dx <= 1; ++dx) {
             const int yy = y + dy, xx = x + dx;
             if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-              S = __fadd_rn(S, px(g, yy * W + xx));
+              S = __fadd_rn(S, sg[yy * W + xx]);
               ++c;
             }
           }

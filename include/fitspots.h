@@ -246,7 +246,8 @@ int fit_spots_last_cuda_error(void);
  *                           largest mean, ties to the lowest row-major index
  *   both                    s0 = sqrt(max(M, 1) / pi), M = #{g > (max g - min g) e^(-1/2) + min g}
  * FP32 throughout; the decisions (the threshold test and the comparison of two means
- * S_i / c_i > S_j / c_j as S_i c_j > S_j c_i) are exact for integer-valued pixels below 2^21.
+ * S_i / c_i > S_j / c_j as S_i c_j > S_j c_i, S summed row by row: each row's neighbours left
+ * to right, then the rows top to bottom) are exact for integer-valued pixels below 2^21.
  * images/offsets/roi_dims as for fit_spots (W, H in 1..32); out_init device float[n][4]; an
  * invalid ROI gets four NaNs. Asynchronous on `stream`.
  */

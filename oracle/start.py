@@ -17,9 +17,10 @@ Readings that fix the precision of the integer decisions (the same as the kernel
 both sides decide alike): the amplitude a0 = max g - min g, the threshold fl(fl(a0 c) + b0)
 with c = e^(-1/2) rounded to FP32 and every product and sum in FP32; a pixel counts in M when
 its FP32 value exceeds that threshold; two neighbourhood means are compared as
-S_i c_j > S_j c_i with S the FP32 sum of the in-ROI neighbours taken in row-major order and c
-their count, the products in FP32. For integer-valued pixels below 2^21 all of these are
-exact. The centroid and sigma0 themselves are computed in FP64 here.
+S_i c_j > S_j c_i with c the neighbour count and S summed in FP32 row by row: each row's
+in-ROI neighbours left to right, then those row sums top to bottom; the products in FP32.
+For integer-valued pixels below 2^21 all of these are exact. The centroid and sigma0
+themselves are computed in FP64 here.
 
 parity unpinned: the zero-weight fallback (ROI centre) and the tie rule of PAPER are
 conventions, not the paper's.
@@ -49,11 +50,14 @@ def start_one(g: np.ndarray, W: int, H: int, rule: int) -> np.ndarray:
                 S = np.float32(0.0)
                 c = 0
                 for dy in (-1, 0, 1):
+                    if not 0 <= y + dy < H:
+                        continue
+                    row = np.float32(0.0)
                     for dx in (-1, 0, 1):
-                        yy, xx = y + dy, x + dx
-                        if 0 <= yy < H and 0 <= xx < W:
-                            S = np.float32(S + img[yy, xx])
+                        if 0 <= x + dx < W:
+                            row = np.float32(row + img[y + dy, x + dx])
                             c += 1
+                    S = np.float32(S + row)
                 if best is None or np.float32(S * np.float32(best[1])) > np.float32(best[0] * np.float32(c)):
                     best = (S, c, x, y)
         x0, y0 = float(best[2]), float(best[3])

@@ -13,9 +13,10 @@
 // Decisions are taken in FP32 on quantities that are exact for integer-valued pixels below
 // 2^21 (uint16 data, photon counts): a0 and the threshold are formed as fl(fl(a0 c) + b0)
 // with c = fl(e^(-1/2)); two neighbourhood means S_i / c_i and S_j / c_j are compared as
-// S_i c_j against S_j c_i, where S is the FP32 sum of the in-ROI neighbours in row-major
-// order. One warp per spot, lanes over the pixels (row-major, 32 apart); the ROI is staged in
-// shared memory once and both passes and the 3 x 3 windows read it there.
+// S_i c_j against S_j c_i. S is separable: the in-ROI row sums of three (left, centre, right,
+// added in that order) of the rows above, at and below (added in that order). One warp per
+// spot, lanes over the pixels (row-major, 32 apart); the ROI and its row sums are staged in
+// shared memory once and both passes and the windows read them there.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -45,7 +46,10 @@ __device__ __forceinline__ float px(const T *p, int i) {
   return (float)__ldg(p + i);
 }
 
-constexpr int kStartWarpFloats = 1024;  // one ROI of at most 32 x 32 pixels per warp
+// per warp: one ROI of <= 32 x 32 pixels, and for the 3 x 3 rule its row sums of three
+__host__ __device__ constexpr int start_warp_floats(int rule) {
+  return rule == FS_START_PAPER ? 2 * 1024 : 1024;
+}
 
 // candidate (mean numerator S, neighbour count c, pixel index i) of the 3 x 3 rule: does a
 // beat b? Larger S / c, ties to the lower index.
@@ -56,8 +60,9 @@ __device__ __forceinline__ bool beats(float Sa, float ca, int ia, float Sb, floa
 
 template <typename T>
 __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
-  __shared__ float sm_all[(kStartThreads / 32) * kStartWarpFloats];
-  float *const sg = sm_all + (threadIdx.x >> 5) * kStartWarpFloats;  // the warp's ROI
+  extern __shared__ float sm_all[];
+  float *const sg = sm_all + (threadIdx.x >> 5) * start_warp_floats(a.rule);  // the warp's ROI
+  float *const sr = sg + 1024;  // its row sums of three (3 x 3 rule only)
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (kStartThreads / 32);
   const T *const img = static_cast<const T *>(a.images);
@@ -94,7 +99,21 @@ __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
     int bi = N;
     // (x, y) of pixel i = lane + 32 k, stepped without divisions
     const int sy = 32 / W, sx = 32 - sy * W;
-    int y = lane / W, x = lane - (lane / W) * W;
+    const int x_start = lane - (lane / W) * W, y_start = lane / W;
+    if (a.rule == FS_START_PAPER) {
+      int x = x_start;
+      for (int i = lane; i < N; i += 32) {
+        float r = 0.f;
+        if (x > 0) r = __fadd_rn(r, sg[i - 1]);
+        r = __fadd_rn(r, sg[i]);
+        if (x < W - 1) r = __fadd_rn(r, sg[i + 1]);
+        sr[i] = r;
+        x += sx;
+        if (x >= W) x -= W;
+      }
+      __syncwarp();
+    }
+    int y = y_start, x = x_start;
     for (int i = lane; i < N; i += 32) {
       const float v = sg[i];
       M += v > thr;
@@ -104,15 +123,10 @@ __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
       swy = fmaf(w, (float)y, swy);
       if (a.rule == FS_START_PAPER) {
         float S = 0.f;
-        int c = 0;
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int yy = y + dy, xx = x + dx;
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-              S = __fadd_rn(S, sg[yy * W + xx]);
-              ++c;
-            }
-          }
+        if (y > 0) S = __fadd_rn(S, sr[i - W]);
+        S = __fadd_rn(S, sr[i]);
+        if (y < H - 1) S = __fadd_rn(S, sr[i + W]);
+        const int c = (1 + (x > 0) + (x < W - 1)) * (1 + (y > 0) + (y < H - 1));
         if (beats(S, (float)c, i, bS, bc, bi)) {
           bS = S;
           bc = (float)c;
@@ -188,11 +202,12 @@ extern "C" int fit_spots_start(const void *images, int dtype, int64_t image_elem
   const int per_block = kStartThreads / 32;
   int64_t blocks = (n + per_block - 1) / per_block;
   if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  const size_t smem = (size_t)per_block * start_warp_floats(rule) * sizeof(float);
   if (dtype == FS_U16)
     start_kernel<unsigned short>
-        <<<(int)blocks, kStartThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+        <<<(int)blocks, kStartThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
   else
-    start_kernel<float><<<(int)blocks, kStartThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    start_kernel<float><<<(int)blocks, kStartThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
   e = cudaGetLastError();
   return e == cudaSuccess ? FS_OK : FS_ERR_CUDA;
 }

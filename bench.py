@@ -355,7 +355,45 @@ def _extras(args, dev, which=("mixed", "backward", "serving", "start")) -> dict:
         out.update(_extra_serving(args, dev))
     if "start" in which:
         out.update(_extra_start(dev, stream, hbm))
+    if "table1" in which:
+        out.update(_extra_table1(dev, stream))
     return out
+
+
+def _extra_table1(dev, stream) -> dict:
+    """The paper's accuracy protocol (Results section, Table 1): 100,000 fits of 9x9 spots
+    per row, timed, with the absolute centre and width errors in units of the true sigma."""
+    import numpy as np
+    from paper_2106_02045_gb300 import fitspots, synth
+    golden = ROOT / "tests" / "golden" / "table1_fit2dgaussian.txt"
+    rows = [[float(v) for v in line.split()] for line in golden.read_text().splitlines()
+            if line.strip() and not line.startswith("#")]
+    res = []
+    for k, (sig, bg, *ref) in enumerate(rows):
+        b = synth.make_paper(100_000, 9, sig, bg, seed=synth.SEED_BASE + 10 + k, device=dev)
+        out = fitspots.alloc_outputs(b.n, dev)
+        ws = _fit_workspace(b.n, dev)
+        ms = _timed(lambda: fitspots.fit_batch(b, out=out, workspace=ws, stream=stream), 3, stream)
+        p = out["params"].cpu().numpy().astype(np.float64)
+        t = b.truth["params"].cpu().numpy()
+        st = t[:, 2]
+        ex = np.concatenate([np.abs(p[:, 0] - t[:, 0]), np.abs(p[:, 1] - t[:, 1])])
+        ex /= np.concatenate([st, st])
+        es = np.abs(np.abs(p[:, 2]) - st) / st
+        it = out["iters"].cpu().numpy()
+        res.append({"signal": sig, "background": bg, "ms": ms, "fits_per_s": b.n / (ms * 1e-3),
+                    "x_err_median_mean_std": [float(np.median(ex)), float(ex.mean()), float(ex.std())],
+                    "sigma_err_median_mean_std": [float(np.median(es)), float(es.mean()), float(es.std())],
+                    "paper_x": ref[:3], "paper_sigma": ref[3:],
+                    "iters_4_or_5": float(np.mean((it == 4) | (it == 5)))})
+    return {"table1": {"workload": "paper protocol: 100,000 fits of 9x9 isotropic spots per row",
+                       "rows": res}}
+
+
+def _fit_workspace(n, dev):
+    import torch
+    from paper_2106_02045_gb300 import fitspots
+    return torch.empty(fitspots.workspace_bytes(n), dtype=torch.uint8, device=dev)
 
 
 def _extra_start(dev, stream, hbm) -> dict:
@@ -538,8 +576,8 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
-    ap.add_argument("--extras", default="mixed,backward,serving,start",
-                    help="comma-separated subset of mixed,backward,serving,start")
+    ap.add_argument("--extras", default="mixed,backward,serving,start,table1",
+                    help="comma-separated subset of mixed,backward,serving,start,table1")
     ap.add_argument("--mixed-spots", type=int, default=2_000_000)
     ap.add_argument("--serving-frames", type=int, default=20000)
     ap.add_argument("--serving-warmup", type=int, default=1000)

@@ -357,7 +357,33 @@ def _extras(args, dev, which=("mixed", "backward", "serving", "start")) -> dict:
         out.update(_extra_start(dev, stream, hbm))
     if "table1" in which:
         out.update(_extra_table1(dev, stream))
+    if "explicit" in which:
+        out.update(_extra_explicit(dev, stream))
     return out
+
+
+def _extra_explicit(dev, stream) -> dict:
+    """Implicit against explicit amplitudes on the same 262,144 ell32 spots: time, LM
+    iterations and evaluated points per spot, share stopped by the iteration budget."""
+    import torch
+    from paper_2106_02045_gb300 import fitspots, synth
+    b = synth.make_workload("ell32", 262_144, device=dev)
+    conv = torch.tensor(CONVERGED, device=dev, dtype=torch.int32)
+    res = {}
+    oi = fitspots.alloc_outputs(b.n, dev)
+    ws = _fit_workspace(b.n, dev)
+    ms = _timed(lambda: fitspots.fit_batch(b, out=oi, workspace=ws, stream=stream), 3, stream)
+    oe = fitspots.alloc_outputs(b.n, dev)
+    mse = _timed(lambda: fitspots.fit_explicit(b.images, b.offsets, b.dims, b.init, b.model,
+                                               out=oe, stream=stream), 3, stream)
+    for name, o, t in (("implicit", oi, ms), ("explicit", oe, mse)):
+        c = torch.isin(o["state"], conv)
+        res[name] = {"ms": t, "converged": float(c.float().mean()),
+                     "iters_per_spot": float(o["iters"].float().mean()),
+                     "evals_per_spot": float(o["evals"].float().mean()),
+                     "at_iteration_budget": float((o["state"] == 0).float().mean())}
+    return {"explicit": {"workload": "ell32: 262,144 spots, the same start values, damping and "
+                                     "stop tests for both methods", **res}}
 
 
 def _extra_table1(dev, stream) -> dict:
@@ -576,8 +602,9 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
-    ap.add_argument("--extras", default="mixed,backward,serving,start,table1",
-                    help="comma-separated subset of mixed,backward,serving,start,table1")
+    ap.add_argument("--extras", default="mixed,backward,serving,start,table1,explicit",
+                    help="comma-separated subset of mixed,backward,serving,start,table1,"
+                         "explicit")
     ap.add_argument("--mixed-spots", type=int, default=2_000_000)
     ap.add_argument("--serving-frames", type=int, default=20000)
     ap.add_argument("--serving-warmup", type=int, default=1000)

@@ -238,6 +238,22 @@ const char *fit_spots_strerror(int code);
 int fit_spots_last_cuda_error(void);
 
 /*
+ * The comparison method for the paper's claim that implicit amplitudes need fewer
+ * iterations: plain Levenberg-Marquardt over (x0, y0, sigma[, sigma_y], alpha, beta) with
+ * h = alpha f + beta and the per-pixel Jacobian (alpha df/dp, f, 1), the same damping
+ * schedule, limit() box on the shape parameters and stop tests as fit_spots (min_step on
+ * the shape parameters), start amplitudes alpha0 = max g - min g, beta0 = min g. Arguments
+ * and outputs as for fit_spots (iterations and evaluations counted the same way); no
+ * workspace; one warp per spot, FP32.
+ */
+int fit_spots_explicit(const void *images, int dtype, int64_t image_elems,
+                       const int64_t *offsets, const int32_t *roi_dims, const float *init_params,
+                       const uint8_t *model, int64_t n, int max_iter, double max_error,
+                       double min_delta, double min_step, float *out_params, float *out_alpha,
+                       float *out_beta, float *out_chi2, int32_t *out_state, int32_t *out_iters,
+                       int32_t *out_evals, void *stream);
+
+/*
  * Start values (x0, y0, s0, s0) for the fit, estimated on the device from each ROI's pixels
  * (the paper estimates start values from the image before fitting, Results section).
  *   rule FS_START_CENTROID  centre = centroid of max(g - min g, 0), the ROI centre

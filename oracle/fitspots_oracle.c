@@ -400,6 +400,200 @@ void or_fit_spots(const void *images, int dtype, int64_t image_elems, const int6
     }
 }
 
+/* ------------------------------------------------------------------ explicit LM
+ * The comparison method of the paper's claim that implicit amplitudes need fewer
+ * iterations (Sec. "Results and Discussion"): plain LM over the full vector
+ * q = (x, y, sigma[, sigma_y], alpha, beta) with the model h_i = alpha f_i + beta, the
+ * per-pixel Jacobian (alpha df_i/dp_j, f_i, 1), the same damping schedule, limit() box on
+ * the shape parameters and stop criteria as or_fit_one. Readings: alpha and beta are not
+ * boxed; the minStep test covers the shape parameters (as for the implicit method, so both
+ * stop on the same criteria); start amplitudes alpha0 = max g - min g, beta0 = min g. */
+static int evaluate_explicit(int model, int W, int H, const double *g, const double *q,
+                             double *chi2, double A[6][6], double b[6])
+{
+    const int N = W * H, P = or_nparams(model), Q = P + 2;
+    double f[OR_MAX_PIXELS], d[4 * OR_MAX_PIXELS];
+    const double p[4] = {q[0], q[1], q[2], P == 4 ? q[3] : q[2]};
+    const double alpha = q[P], beta = q[P + 1];
+    or_profile(model, W, H, p, f, A ? d : NULL);
+    double c2 = 0.0;
+    if (A)
+        for (int j = 0; j < Q; ++j) {
+            b[j] = 0.0;
+            for (int k = 0; k < Q; ++k) A[j][k] = 0.0;
+        }
+    for (int i = 0; i < N; ++i) {
+        const double r = g[i] - (alpha * f[i] + beta);
+        c2 += r * r;
+        if (!A) continue;
+        double J[6];
+        for (int j = 0; j < P; ++j) J[j] = alpha * d[(size_t)j * N + i];
+        J[P] = f[i];
+        J[P + 1] = 1.0;
+        for (int j = 0; j < Q; ++j) {
+            b[j] += J[j] * r;
+            for (int k = 0; k < Q; ++k) A[j][k] += J[j] * J[k];
+        }
+    }
+    *chi2 = c2;
+    return isfinite(c2) ? 0 : -1;
+}
+
+/* Eq. 14 for up to 6 unknowns: (A + lambda diag A) delta = b by Cholesky. */
+static int solve_damped6(int Q, double A[6][6], const double *b, double lambda, double *delta)
+{
+    double L[6][6] = {{0}}, y[6];
+    for (int j = 0; j < Q; ++j) {
+        double s = A[j][j] * (1.0 + lambda);
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        if (!(s > 0.0) || !isfinite(s)) return -1;
+        L[j][j] = sqrt(s);
+        for (int i = j + 1; i < Q; ++i) {
+            double t = A[i][j];
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    for (int j = 0; j < Q; ++j) {
+        double t = b[j];
+        for (int k = 0; k < j; ++k) t -= L[j][k] * y[k];
+        y[j] = t / L[j][j];
+    }
+    for (int j = Q - 1; j >= 0; --j) {
+        double t = y[j];
+        for (int k = j + 1; k < Q; ++k) t -= L[k][j] * delta[k];
+        delta[j] = t / L[j][j];
+    }
+    for (int j = 0; j < Q; ++j)
+        if (!isfinite(delta[j])) return -1;
+    return 0;
+}
+
+static double trial_explicit(int model, int W, int H, const double *g, const double *best,
+                             const double *delta, double *qt)
+{
+    const int P = or_nparams(model), Q = P + 2;
+    double p[4];
+    for (int j = 0; j < Q; ++j) qt[j] = best[j] + delta[j];
+    p[0] = qt[0];
+    p[1] = qt[1];
+    p[2] = qt[2];
+    p[3] = P == 4 ? qt[3] : qt[2];
+    or_limit(model, W, H, p);
+    for (int j = 0; j < P; ++j) qt[j] = p[j];
+    double c2;
+    if (evaluate_explicit(model, W, H, g, qt, &c2, NULL, NULL)) return NAN;
+    return c2;
+}
+
+int or_fit_explicit_one(int model, int W, int H, const double *g, const double *p0,
+                        int max_iter, double max_error, double min_delta, double min_step,
+                        double *p_out, double *alpha_out, double *beta_out, double *chi2n_out,
+                        int *iters_out, int *evals_out)
+{
+    const int P = or_nparams(model), Q = P + 2, N = W * H;
+    double p[4] = {p0[0], p0[1], p0[2], P == 4 ? p0[3] : p0[2]};
+    or_limit(model, W, H, p);
+    double gmin = g[0], gmax = g[0];
+    for (int i = 1; i < N; ++i) {
+        if (g[i] < gmin) gmin = g[i];
+        if (g[i] > gmax) gmax = g[i];
+    }
+    double q[6], best[6], delta[6], qt[6], A[6][6], b[6];
+    for (int j = 0; j < P; ++j) q[j] = p[j];
+    q[P] = gmax - gmin;
+    q[P + 1] = gmin;
+
+    int k_lambda = -2, it = 0, evals = 0, state = OR_MAX_ITER;
+    while (it < max_iter) {
+        ++it;
+        double chi;
+        ++evals;
+        if (evaluate_explicit(model, W, H, g, q, &chi, A, b)) chi = NAN;
+        if (isnan(chi)) { state = OR_NOT_CONVERGED; break; }
+        if (chi < max_error) { state = OR_MAX_ERROR; break; }
+        memcpy(best, q, sizeof best);
+        double Chi;
+        if (solve_damped6(Q, A, b, pow(10.0, k_lambda), delta)) { state = OR_NOT_CONVERGED; break; }
+        ++evals;
+        Chi = trial_explicit(model, W, H, g, best, delta, qt);
+        if (chi > Chi) --k_lambda;
+        int failed_solve = 0;
+        while (!all_small(P, delta, best, min_step) && chi < Chi && k_lambda < 4) {
+            ++k_lambda;
+            if (solve_damped6(Q, A, b, pow(10.0, k_lambda), delta)) { failed_solve = 1; break; }
+            ++evals;
+            Chi = trial_explicit(model, W, H, g, best, delta, qt);
+        }
+        if (failed_solve) { state = OR_NOT_CONVERGED; break; }
+        if (chi < Chi || isnan(Chi)) {
+            state = (all_small(P, delta, best, min_step) && !isnan(Chi)) ? OR_NO_DECREASE
+                                                                         : OR_NOT_CONVERGED;
+            break;
+        }
+        memcpy(q, qt, sizeof q);
+        if (Chi < max_error) { state = OR_MAX_ERROR; break; }
+        if (chi * (1.0 - min_delta) < Chi) { state = OR_MIN_DELTA; break; }
+        if (all_small(P, delta, best, min_step)) { state = OR_MIN_STEP; break; }
+    }
+    double chi;
+    if (evaluate_explicit(model, W, H, g, q, &chi, NULL, NULL)) chi = NAN;
+    for (int j = 0; j < 4; ++j) p_out[j] = j < P ? q[j] : q[2];
+    *alpha_out = q[P];
+    *beta_out = q[P + 1];
+    *chi2n_out = chi / (double)(N - P - 2);
+    *iters_out = it;
+    *evals_out = evals;
+    return state;
+}
+
+void or_fit_spots_explicit(const void *images, int dtype, int64_t image_elems,
+                           const int64_t *offsets, const int32_t *dims, const float *init,
+                           const uint8_t *model, int64_t n, int max_iter, double max_error,
+                           double min_delta, double min_step, double *out_params,
+                           double *out_alpha, double *out_beta, double *out_chi2,
+                           int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                           int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < n; ++s) {
+        const int W = dims[2 * s], H = dims[2 * s + 1], m = model[s];
+        const int64_t off = offsets[s];
+        double p0[4] = {init[4 * s], init[4 * s + 1], init[4 * s + 2], init[4 * s + 3]};
+        const int N = W * H;
+        if (!(m == OR_MODEL_ISO || m == OR_MODEL_ELLIPTIC) || W < 3 || H < 3 ||
+            W > OR_MAX_SIDE || H > OR_MAX_SIDE || N <= or_nparams(m) + 2 || off < 0 ||
+            off + N > image_elems) {
+            for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p0[j];
+            out_alpha[s] = out_beta[s] = out_chi2[s] = NAN;
+            out_state[s] = OR_INVALID;
+            out_iters[s] = 0;
+            if (out_evals) out_evals[s] = 0;
+            continue;
+        }
+        double g[OR_MAX_PIXELS];
+        for (int i = 0; i < N; ++i) {
+            if (dtype == OR_U16) g[i] = (double)((const uint16_t *)images)[off + i];
+            else if (dtype == OR_F32) g[i] = (double)((const float *)images)[off + i];
+            else g[i] = ((const double *)images)[off + i];
+        }
+        double p[4], a, b, c2n;
+        int it, ev;
+        const int st = or_fit_explicit_one(m, W, H, g, p0, max_iter, max_error, min_delta,
+                                           min_step, p, &a, &b, &c2n, &it, &ev);
+        for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p[j];
+        out_alpha[s] = a;
+        out_beta[s] = b;
+        out_chi2[s] = c2n;
+        out_state[s] = st;
+        out_iters[s] = it;
+        if (out_evals) out_evals[s] = ev;
+    }
+}
+
 /* Pin helper: alpha^, beta^, chi^2 (Eq. 2, 6) and optionally J^T J, J^T (g-h) at p for
  * one spot given as doubles. Returns 0 or -1. */
 int or_evaluate(int model, int W, int H, const double *g, const double *p, double *alpha,

@@ -41,6 +41,9 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_uniform.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
                                           vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fit_spots_uniform.restype = i
+        lib.fit_spots_explicit.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
+                                           vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.fit_spots_explicit.restype = i
         lib.fit_spots_start.argtypes = [vp, i, i64, vp, vp, i64, i, vp, vp]
         lib.fit_spots_start.restype = i
         lib.fit_spots_uniform_host.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
@@ -246,6 +249,34 @@ def fit_uniform_host(images: torch.Tensor, width: int, height: int, model: int,
             _ptr(o["iters"]), _ptr(o.get("evals")), int(chunk), _ptr(workspace),
             workspace.numel(), ctypes.c_void_p(s.cuda_stream))
     check(rc, "fit_spots_uniform_host")
+    return o
+
+
+def fit_explicit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
+                 init: torch.Tensor, model: torch.Tensor, *, max_iter: int = 20,
+                 max_error: float = 0.0, min_delta: float = 1e-6, min_step: float = 1e-4,
+                 out: dict | None = None, stream: torch.cuda.Stream | None = None) -> dict:
+    """The explicit-amplitude LM (comparison method), same arguments and outputs as fit."""
+    dev = images.device
+    if dev.type != "cuda":
+        raise FitSpotsError("images must be a CUDA tensor")
+    dtype = U16 if images.dtype == torch.uint16 else F32 if images.dtype == torch.float32 else None
+    if dtype is None:
+        raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
+    _need(offsets, torch.int64, "offsets", dev)
+    _need(dims, torch.int32, "dims", dev)
+    _need(init, torch.float32, "init", dev)
+    _need(model, torch.uint8, "model", dev)
+    n = offsets.numel()
+    o = out if out is not None else alloc_outputs(n, dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = library().fit_spots_explicit(
+            _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(init),
+            _ptr(model), n, int(max_iter), float(max_error), float(min_delta), float(min_step),
+            _ptr(o["params"]), _ptr(o["alpha"]), _ptr(o["beta"]), _ptr(o["chi2"]), _ptr(o["state"]),
+            _ptr(o["iters"]), _ptr(o.get("evals")), ctypes.c_void_p(s.cuda_stream))
+    check(rc, "fit_spots_explicit")
     return o
 
 

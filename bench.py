@@ -5,12 +5,15 @@ synthetic camera data) through ``fit_spots_uniform``, inputs resident in HBM (2 
 than L2, so no flush is needed between steps). The JSON line reports:
 
 * value        converged fits per second, kernel timed with CUDA events on its stream
-* e2e          the same metric through the public API from pinned host buffers, with the
-               H2D copy of the step's pixels and start values and the D2H copy of all
-               per-spot results inside the timed region
+* e2e          the same metric through the host-buffer call (fit_spots_uniform_host) from
+               pinned host memory: the H2D copies of the step's pixels and start values and
+               the D2H copies of all per-spot results are inside the timed region,
+               overlapped with the fits chunk by chunk
 * roofline     the fit kernel against the FP32 lane-op peak (152 SMs x 128 lanes x max
                clock), counting 7 algorithmic FP32 operations per pixel per evaluated
-               point (see the design doc for the derivation)
+               point (the separable evaluation: 1 FMA in the amplitude pass, 6 operations in
+               the residual pass); direct_count repeats it with the work of a per-pixel
+               implementation (12 per evaluated point plus 26 per gradient point)
 * cpu_baseline the FP64 oracle on the host cores, timed on a bounded sample of spots
 
 ``--impl reference`` times the oracle itself as the reference arm (host cores only).

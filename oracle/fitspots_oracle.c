@@ -23,7 +23,7 @@
  *                                                   Sec. "Results and Discussion".
  * The Jacobian is formed explicitly pixel by pixel (Eq. 9 form); no sum expansion.
  *
- * Readings where the paper is silent or garbled (each one also listed in the design doc):
+ * Readings where the paper is silent or garbled (the CUDA path follows the same ones):
  *   R1  Eq. 12 sign: J = dh/dp, right-hand side J^T (g - h), p' = p + delta.
  *   R2  Eq. 13 "Jacobian" is the per-pixel J_ij = dh_i/dp_j; J^T J is P x P.
  *   R3  inside the lambda-escalation loop the re-evaluated error is the trial error.

@@ -37,7 +37,7 @@ def test_explicit_matches_oracle(name, n):
     img = synth.as_numpy_images(b)
     ref = oracle.fit_spots_explicit(img, d["offsets"], d["dims"], d["init"], d["model"])
     out = _explicit_gpu(b)
-    # determined spots of the (common) minimum, judged by the implicit oracle fit
+    # determined spots of the (common) minimum, selected with the implicit oracle fit
     imp = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"])
     det = determined(b, imp) & np.isin(ref["state"], CONV)
     agree = np.isin(out["state"], CONV) == np.isin(ref["state"], CONV)

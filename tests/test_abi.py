@@ -115,6 +115,24 @@ def test_host_call_argument_checks(lib):
     assert call(max_iter=0) == -4
 
 
+def test_start_and_explicit_argument_checks(lib):
+    """fit_spots_start and fit_spots_explicit reject malformed calls before any CUDA work."""
+    fake = ctypes.c_void_p(0x1000)
+
+    def start(n=10, dtype=0, rule=0, elems=100, images=fake, out=fake):
+        return lib.fit_spots_start(images, dtype, elems, fake, fake, n, rule, out, None)
+    assert start(n=-1) == -2 and start(elems=-1) == -2 and start(dtype=4) == -3
+    assert start(rule=2) == -8 and start(n=0) == 0
+    assert start(images=None) == -1 and start(out=None) == -1
+
+    def explicit(n=10, max_iter=20, min_delta=1e-6, images=fake, state=fake):
+        return lib.fit_spots_explicit(images, 0, 100, fake, fake, fake, fake, n, max_iter, 0.0,
+                                      min_delta, 1e-4, fake, fake, fake, fake, state, fake,
+                                      None, None)
+    assert explicit(n=-1) == -2 and explicit(max_iter=0) == -4 and explicit(min_delta=1.0) == -5
+    assert explicit(n=0) == 0 and explicit(images=None) == -1 and explicit(state=None) == -1
+
+
 def test_size_classes_and_configs(lib):
     from paper_2106_02045_gb300 import fitspots
     assert lib.fit_spots_num_classes() == 16

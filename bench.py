@@ -362,7 +362,34 @@ def _extras(args, dev, which=("mixed", "backward", "serving", "start")) -> dict:
         out.update(_extra_table1(dev, stream))
     if "explicit" in which:
         out.update(_extra_explicit(dev, stream))
+    if "weighted" in which:
+        out.update(_extra_weighted(dev, stream))
     return out
+
+
+def _extra_weighted(dev, stream) -> dict:
+    """Variance-weighted against unweighted implicit fits on 100,000 iso15 spots (peak 1000,
+    background 100): time, and centre and width errors in units of the true sigma."""
+    import numpy as np
+    from paper_2106_02045_gb300 import fitspots, synth
+    b = synth.make_iso(100_000, 15, 7.0, synth.SEED_BASE + 51, device=dev, name="iso15")
+    t = b.truth["params"].cpu().numpy()
+    res = {}
+    o = fitspots.alloc_outputs(b.n, dev)
+    ws = _fit_workspace(b.n, dev)
+    for name, run in (("unweighted", lambda: fitspots.fit_batch(b, out=o, workspace=ws,
+                                                                  stream=stream)),
+                      ("weighted", lambda: fitspots.fit_weighted(b.images, b.offsets, b.dims,
+                                                                 b.init, b.model, out=o,
+                                                                 stream=stream))):
+        ms = _timed(run, 3, stream)
+        p = o["params"].cpu().numpy().astype(np.float64)
+        c = np.isin(o["state"].cpu().numpy(), CONVERGED)
+        res[name] = {"ms": ms, "converged": float(c.mean()),
+                     "x_err_rms": float(np.sqrt(np.mean(((p[c, 0] - t[c, 0]) / t[c, 2]) ** 2))),
+                     "sigma_err_rms": float(np.sqrt(np.mean(((p[c, 2] - t[c, 2]) / t[c, 2]) ** 2)))}
+    return {"weighted": {"workload": "iso15-like: 100,000 spots of 15x15, peak 1000, background "
+                                     "100, Poisson", **res}}
 
 
 def _extra_explicit(dev, stream) -> dict:
@@ -605,9 +632,9 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
-    ap.add_argument("--extras", default="mixed,backward,serving,start,table1,explicit",
+    ap.add_argument("--extras", default="mixed,backward,serving,start,table1,explicit,weighted",
                     help="comma-separated subset of mixed,backward,serving,start,table1,"
-                         "explicit")
+                         "explicit,weighted")
     ap.add_argument("--mixed-spots", type=int, default=2_000_000)
     ap.add_argument("--serving-frames", type=int, default=20000)
     ap.add_argument("--serving-warmup", type=int, default=1000)

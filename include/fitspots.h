@@ -254,6 +254,20 @@ int fit_spots_explicit(const void *images, int dtype, int64_t image_elems,
                        int32_t *out_evals, void *stream);
 
 /*
+ * Variance-weighted implicit-amplitude fit: minimises sum w_i (g_i - alpha f_i - beta)^2 with
+ * w_i = 1 / max(g_i, 1) (Poisson variance from the data), alpha and beta from the weighted
+ * Eq. 5-6 at every evaluated point, the same damping schedule, box and stop tests as
+ * fit_spots; out_chi2 is the weighted chi^2 / (N - P - 2). Arguments and outputs as for
+ * fit_spots; no workspace; one warp per spot, FP32.
+ */
+int fit_spots_weighted(const void *images, int dtype, int64_t image_elems,
+                       const int64_t *offsets, const int32_t *roi_dims, const float *init_params,
+                       const uint8_t *model, int64_t n, int max_iter, double max_error,
+                       double min_delta, double min_step, float *out_params, float *out_alpha,
+                       float *out_beta, float *out_chi2, int32_t *out_state, int32_t *out_iters,
+                       int32_t *out_evals, void *stream);
+
+/*
  * Start values (x0, y0, s0, s0) for the fit, estimated on the device from each ROI's pixels
  * (the paper estimates start values from the image before fitting, Results section).
  *   rule FS_START_CENTROID  centre = centroid of max(g - min g, 0), the ROI centre

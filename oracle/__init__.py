@@ -52,6 +52,9 @@ def _load():
         lib.or_fit_spots_explicit.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
                                               vp, vp, vp, vp, vp, vp, vp, i]
         lib.or_fit_spots_explicit.restype = None
+        lib.or_fit_spots_weighted.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
+                                              vp, vp, vp, vp, vp, vp, vp, i, i]
+        lib.or_fit_spots_weighted.restype = None
         lib.or_evaluate.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp, vp]
         lib.or_evaluate.restype = i
         lib.or_profile.argtypes = [i, i, i, vp, vp, vp]
@@ -210,6 +213,30 @@ def fit_spots_explicit(images: np.ndarray, offsets, dims, init, model, *, max_it
                               float(min_step), _p(out["params"]), _p(out["alpha"]),
                               _p(out["beta"]), _p(out["chi2"]), _p(out["state"]),
                               _p(out["iters"]), _p(out["evals"]), int(nthreads))
+    return out
+
+
+def fit_spots_weighted(images: np.ndarray, offsets, dims, init, model, *, max_iter: int = 20,
+                       max_error: float = 0.0, min_delta: float = 1e-6, min_step: float = 1e-4,
+                       unit_weights: bool = False, nthreads: int = 0) -> dict:
+    """The variance-weighted implicit-amplitude fit (weights 1 / max(g, 1), or all 1)."""
+    lib = _load()
+    images = np.ascontiguousarray(images)
+    dtype = {np.dtype(np.uint16): U16, np.dtype(np.float32): F32,
+             np.dtype(np.float64): F64}[images.dtype]
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    dims = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 2)
+    init = np.ascontiguousarray(init, dtype=np.float32).reshape(-1, 4)
+    model = np.ascontiguousarray(model, dtype=np.uint8)
+    n = offsets.size
+    out = dict(params=np.empty((n, 4)), alpha=np.empty(n), beta=np.empty(n), chi2=np.empty(n),
+               state=np.empty(n, np.int32), iters=np.empty(n, np.int32),
+               evals=np.empty(n, np.int32))
+    lib.or_fit_spots_weighted(_p(images), dtype, images.size, _p(offsets), _p(dims), _p(init),
+                              _p(model), n, int(max_iter), float(max_error), float(min_delta),
+                              float(min_step), _p(out["params"]), _p(out["alpha"]),
+                              _p(out["beta"]), _p(out["chi2"]), _p(out["state"]),
+                              _p(out["iters"]), _p(out["evals"]), int(unit_weights), int(nthreads))
     return out
 
 

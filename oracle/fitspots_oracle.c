@@ -594,6 +594,199 @@ void or_fit_spots_explicit(const void *images, int dtype, int64_t image_elems,
     }
 }
 
+/* ------------------------------------------------------------------ weighted fit
+ * A variance-weighted variant (the paper notes that its residuals are unweighted and gives
+ * no weighted method; readings): chi^2_w = sum w_i (g_i - h_i)^2 with w_i = 1 / max(g_i, 1),
+ * the Poisson variance estimated from the data (Neyman's chi^2). The implicit amplitudes
+ * solve the weighted normal equations of Eq. 5-6,
+ *   [Sff Sf; Sf Sw] (alpha, beta) = (Sfg, Sg),  Sw = sum w, Sf = sum w f, Sff = sum w f^2,
+ *   Sg = sum w g, Sfg = sum w f g,
+ * their derivatives follow Eq. 7-8 with the same weights, J_ij = dh_i/dp_j as in Eq. 9, and
+ * the LM step uses J^T W J and J^T W (g - h). Damping schedule, box and stop tests as
+ * or_fit_one; with unit weights this is exactly the unweighted fit. */
+static int weighted_jacobian(int model, int W, int H, const double *g, const double *w,
+                             const double *p, double *f, double *J, double *alpha, double *beta)
+{
+    const int N = W * H, P = or_nparams(model);
+    double d[4 * OR_MAX_PIXELS];
+    or_profile(model, W, H, p, f, J ? d : NULL);
+    double Sw = 0.0, Sf = 0.0, Sff = 0.0, Sg = 0.0, Sfg = 0.0;
+    for (int i = 0; i < N; ++i) {
+        Sw += w[i];
+        Sf += w[i] * f[i];
+        Sff += w[i] * f[i] * f[i];
+        Sg += w[i] * g[i];
+        Sfg += w[i] * f[i] * g[i];
+    }
+    const double D = Sw * Sff - Sf * Sf;
+    if (!(D > 0.0) || !isfinite(D)) return -1;
+    const double a = (Sw * Sfg - Sf * Sg) / D, b = (Sff * Sg - Sf * Sfg) / D;
+    *alpha = a;
+    *beta = b;
+    if (!J) return 0;
+    for (int j = 0; j < P; ++j) {
+        const double *dj = d + (size_t)j * N;
+        double dSf = 0.0, dSff = 0.0, dSfg = 0.0;
+        for (int i = 0; i < N; ++i) {
+            dSf += w[i] * dj[i];
+            dSff += 2.0 * w[i] * f[i] * dj[i];
+            dSfg += w[i] * g[i] * dj[i];
+        }
+        /* differentiate Sff a + Sf b = Sfg and Sf a + Sw b = Sg in p_j */
+        const double r1 = dSfg - dSff * a - dSf * b, r2 = -dSf * a;
+        const double da = (Sw * r1 - Sf * r2) / D, db = (Sff * r2 - Sf * r1) / D;
+        for (int i = 0; i < N; ++i) J[(size_t)j * N + i] = da * f[i] + a * dj[i] + db;
+    }
+    return 0;
+}
+
+static int evaluate_weighted(int model, int W, int H, const double *g, const double *w,
+                             const double *p, double *alpha, double *beta, double *chi2,
+                             double A[4][4], double b[4])
+{
+    const int N = W * H, P = or_nparams(model);
+    double f[OR_MAX_PIXELS], J[4 * OR_MAX_PIXELS];
+    if (weighted_jacobian(model, W, H, g, w, p, f, A ? J : NULL, alpha, beta)) return -1;
+    double c2 = 0.0, r[OR_MAX_PIXELS];
+    for (int i = 0; i < N; ++i) {
+        r[i] = g[i] - (*alpha * f[i] + *beta);
+        c2 += w[i] * r[i] * r[i];
+    }
+    *chi2 = c2;
+    if (!A) return 0;
+    for (int j = 0; j < P; ++j) {
+        double bj = 0.0;
+        for (int i = 0; i < N; ++i) bj += J[(size_t)j * N + i] * w[i] * r[i];
+        b[j] = bj;
+        for (int k = 0; k < P; ++k) {
+            double ajk = 0.0;
+            for (int i = 0; i < N; ++i) ajk += J[(size_t)j * N + i] * w[i] * J[(size_t)k * N + i];
+            A[j][k] = ajk;
+        }
+    }
+    return 0;
+}
+
+static double trial_weighted(int model, int W, int H, const double *g, const double *w,
+                             const double *best, const double *delta, double *pt)
+{
+    const int P = or_nparams(model);
+    pt[0] = best[0] + delta[0];
+    pt[1] = best[1] + delta[1];
+    pt[2] = best[2] + delta[2];
+    pt[3] = P == 4 ? best[3] + delta[3] : pt[2];
+    or_limit(model, W, H, pt);
+    if (P == 3) pt[3] = pt[2];
+    double a, bb, c2;
+    if (evaluate_weighted(model, W, H, g, w, pt, &a, &bb, &c2, NULL, NULL)) return NAN;
+    return c2;
+}
+
+/* weights: NULL for 1 / max(g, 1), or one per pixel */
+int or_fit_weighted_one(int model, int W, int H, const double *g, const double *weights,
+                        const double *p0, int max_iter, double max_error, double min_delta,
+                        double min_step, double *p_out, double *alpha_out, double *beta_out,
+                        double *chi2n_out, int *iters_out, int *evals_out)
+{
+    const int P = or_nparams(model), N = W * H;
+    double w[OR_MAX_PIXELS];
+    for (int i = 0; i < N; ++i) w[i] = weights ? weights[i] : 1.0 / (g[i] > 1.0 ? g[i] : 1.0);
+    double p[4] = {p0[0], p0[1], p0[2], P == 4 ? p0[3] : p0[2]};
+    or_limit(model, W, H, p);
+    if (P == 3) p[3] = p[2];
+    int k_lambda = -2, it = 0, evals = 0, state = OR_MAX_ITER;
+    double A[4][4], b[4], best[4], delta[4], pt[4];
+    while (it < max_iter) {
+        ++it;
+        double a, bb, chi;
+        ++evals;
+        if (evaluate_weighted(model, W, H, g, w, p, &a, &bb, &chi, A, b)) chi = NAN;
+        if (isnan(chi)) { state = OR_NOT_CONVERGED; break; }
+        if (chi < max_error) { state = OR_MAX_ERROR; break; }
+        memcpy(best, p, sizeof best);
+        double Chi;
+        if (solve_damped(P, A, b, pow(10.0, k_lambda), delta)) { state = OR_NOT_CONVERGED; break; }
+        ++evals;
+        Chi = trial_weighted(model, W, H, g, w, best, delta, pt);
+        if (chi > Chi) --k_lambda;
+        int failed_solve = 0;
+        while (!all_small(P, delta, best, min_step) && chi < Chi && k_lambda < 4) {
+            ++k_lambda;
+            if (solve_damped(P, A, b, pow(10.0, k_lambda), delta)) { failed_solve = 1; break; }
+            ++evals;
+            Chi = trial_weighted(model, W, H, g, w, best, delta, pt);
+        }
+        if (failed_solve) { state = OR_NOT_CONVERGED; break; }
+        if (chi < Chi || isnan(Chi)) {
+            state = (all_small(P, delta, best, min_step) && !isnan(Chi)) ? OR_NO_DECREASE
+                                                                         : OR_NOT_CONVERGED;
+            break;
+        }
+        memcpy(p, pt, sizeof p);
+        if (Chi < max_error) { state = OR_MAX_ERROR; break; }
+        if (chi * (1.0 - min_delta) < Chi) { state = OR_MIN_DELTA; break; }
+        if (all_small(P, delta, best, min_step)) { state = OR_MIN_STEP; break; }
+    }
+    double a, bb, chi;
+    if (evaluate_weighted(model, W, H, g, w, p, &a, &bb, &chi, NULL, NULL)) { a = bb = chi = NAN; }
+    for (int j = 0; j < 4; ++j) p_out[j] = p[j];
+    *alpha_out = a;
+    *beta_out = bb;
+    *chi2n_out = chi / (double)(N - P - 2);
+    *iters_out = it;
+    *evals_out = evals;
+    return state;
+}
+
+void or_fit_spots_weighted(const void *images, int dtype, int64_t image_elems,
+                           const int64_t *offsets, const int32_t *dims, const float *init,
+                           const uint8_t *model, int64_t n, int max_iter, double max_error,
+                           double min_delta, double min_step, double *out_params,
+                           double *out_alpha, double *out_beta, double *out_chi2,
+                           int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                           int unit_weights, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < n; ++s) {
+        const int W = dims[2 * s], H = dims[2 * s + 1], m = model[s];
+        const int64_t off = offsets[s];
+        double p0[4] = {init[4 * s], init[4 * s + 1], init[4 * s + 2], init[4 * s + 3]};
+        const int N = W * H;
+        if (!(m == OR_MODEL_ISO || m == OR_MODEL_ELLIPTIC) || W < 3 || H < 3 ||
+            W > OR_MAX_SIDE || H > OR_MAX_SIDE || N <= or_nparams(m) + 2 || off < 0 ||
+            off + N > image_elems) {
+            for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p0[j];
+            out_alpha[s] = out_beta[s] = out_chi2[s] = NAN;
+            out_state[s] = OR_INVALID;
+            out_iters[s] = 0;
+            if (out_evals) out_evals[s] = 0;
+            continue;
+        }
+        double g[OR_MAX_PIXELS], ones[OR_MAX_PIXELS];
+        for (int i = 0; i < N; ++i) {
+            if (dtype == OR_U16) g[i] = (double)((const uint16_t *)images)[off + i];
+            else if (dtype == OR_F32) g[i] = (double)((const float *)images)[off + i];
+            else g[i] = ((const double *)images)[off + i];
+            ones[i] = 1.0;
+        }
+        double p[4], a, b, c2n;
+        int it, ev;
+        const int st = or_fit_weighted_one(m, W, H, g, unit_weights ? ones : NULL, p0, max_iter,
+                                           max_error, min_delta, min_step, p, &a, &b, &c2n,
+                                           &it, &ev);
+        for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p[j];
+        out_alpha[s] = a;
+        out_beta[s] = b;
+        out_chi2[s] = c2n;
+        out_state[s] = st;
+        out_iters[s] = it;
+        if (out_evals) out_evals[s] = ev;
+    }
+}
+
 /* Pin helper: alpha^, beta^, chi^2 (Eq. 2, 6) and optionally J^T J, J^T (g-h) at p for
  * one spot given as doubles. Returns 0 or -1. */
 int or_evaluate(int model, int W, int H, const double *g, const double *p, double *alpha,

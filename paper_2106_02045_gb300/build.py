@@ -12,7 +12,8 @@ from pathlib import Path
 PKG = Path(__file__).resolve().parent
 ROOT = PKG.parent
 SOURCES = [PKG / "csrc" / "fitspots.cu", PKG / "csrc" / "backward.cu", PKG / "csrc" / "serving.cu",
-           PKG / "csrc" / "start.cu", PKG / "csrc" / "explicit.cu"]
+           PKG / "csrc" / "start.cu", PKG / "csrc" / "explicit.cu",
+           PKG / "csrc" / "weighted.cu"]
 HEADERS = [ROOT / "include" / "fitspots.h"]
 LIB = PKG / "_build" / "libfitspots.so"
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

@@ -44,6 +44,8 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_explicit.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
                                            vp, vp, vp, vp, vp, vp, vp, vp]
         lib.fit_spots_explicit.restype = i
+        lib.fit_spots_weighted.argtypes = lib.fit_spots_explicit.argtypes
+        lib.fit_spots_weighted.restype = i
         lib.fit_spots_start.argtypes = [vp, i, i64, vp, vp, i64, i, vp, vp]
         lib.fit_spots_start.restype = i
         lib.fit_spots_uniform_host.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
@@ -255,7 +257,8 @@ def fit_uniform_host(images: torch.Tensor, width: int, height: int, model: int,
 def fit_explicit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
                  init: torch.Tensor, model: torch.Tensor, *, max_iter: int = 20,
                  max_error: float = 0.0, min_delta: float = 1e-6, min_step: float = 1e-4,
-                 out: dict | None = None, stream: torch.cuda.Stream | None = None) -> dict:
+                 out: dict | None = None, stream: torch.cuda.Stream | None = None,
+                 _entry: str = "fit_spots_explicit") -> dict:
     """The explicit-amplitude LM (comparison method), same arguments and outputs as fit."""
     dev = images.device
     if dev.type != "cuda":
@@ -271,13 +274,20 @@ def fit_explicit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor
     o = out if out is not None else alloc_outputs(n, dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     with torch.cuda.device(dev):
-        rc = library().fit_spots_explicit(
+        rc = getattr(library(), _entry)(
             _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(init),
             _ptr(model), n, int(max_iter), float(max_error), float(min_delta), float(min_step),
             _ptr(o["params"]), _ptr(o["alpha"]), _ptr(o["beta"]), _ptr(o["chi2"]), _ptr(o["state"]),
             _ptr(o["iters"]), _ptr(o.get("evals")), ctypes.c_void_p(s.cuda_stream))
-    check(rc, "fit_spots_explicit")
+    check(rc, _entry)
     return o
+
+
+def fit_weighted(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
+                 init: torch.Tensor, model: torch.Tensor, **kw) -> dict:
+    """The variance-weighted implicit-amplitude fit (weights 1 / max(g, 1)); same arguments
+    and outputs as fit (chi2 is the weighted one)."""
+    return fit_explicit(images, offsets, dims, init, model, _entry="fit_spots_weighted", **kw)
 
 
 START_CENTROID, START_PAPER = 0, 1

@@ -116,7 +116,8 @@ def test_host_call_argument_checks(lib):
 
 
 def test_start_and_explicit_argument_checks(lib):
-    """fit_spots_start and fit_spots_explicit reject malformed calls before any CUDA work."""
+    """fit_spots_start, fit_spots_explicit and fit_spots_weighted reject malformed calls
+    before any CUDA work."""
     fake = ctypes.c_void_p(0x1000)
 
     def start(n=10, dtype=0, rule=0, elems=100, images=fake, out=fake):
@@ -125,12 +126,12 @@ def test_start_and_explicit_argument_checks(lib):
     assert start(rule=2) == -8 and start(n=0) == 0
     assert start(images=None) == -1 and start(out=None) == -1
 
-    def explicit(n=10, max_iter=20, min_delta=1e-6, images=fake, state=fake):
-        return lib.fit_spots_explicit(images, 0, 100, fake, fake, fake, fake, n, max_iter, 0.0,
-                                      min_delta, 1e-4, fake, fake, fake, fake, state, fake,
-                                      None, None)
-    assert explicit(n=-1) == -2 and explicit(max_iter=0) == -4 and explicit(min_delta=1.0) == -5
-    assert explicit(n=0) == 0 and explicit(images=None) == -1 and explicit(state=None) == -1
+    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted):
+        def call(n=10, max_iter=20, min_delta=1e-6, images=fake, state=fake):
+            return fn(images, 0, 100, fake, fake, fake, fake, n, max_iter, 0.0, min_delta, 1e-4,
+                      fake, fake, fake, fake, state, fake, None, None)
+        assert call(n=-1) == -2 and call(max_iter=0) == -4 and call(min_delta=1.0) == -5
+        assert call(n=0) == 0 and call(images=None) == -1 and call(state=None) == -1
 
 
 def test_size_classes_and_configs(lib):

@@ -15,6 +15,7 @@ slot waits in a bounded queue; beyond ``queue_limit`` it is rejected (counted in
 from __future__ import annotations
 
 import collections
+import gc
 import ctypes
 import time
 from dataclasses import dataclass, field
@@ -235,17 +236,25 @@ class TrackingServer:
 
 def run_stream(server: TrackingServer, session: int, host_frames: torch.Tensor, n_frames: int,
                fps: float, t0: float | None = None) -> None:
-    """Feed frames of one session at ``fps`` (arrival = scheduled time) and serve them."""
+    """Feed frames of one session at ``fps`` (arrival = scheduled time) and serve them.
+    Python's cyclic garbage collector is paused meanwhile: a collection of the loop's
+    short-lived objects can stall the host for longer than the queue's 32 ms at 2000 fps."""
     t0 = time.perf_counter() if t0 is None else t0
     period = 1.0 / fps
     ring = host_frames.shape[0]
     k = 0
-    while k < n_frames or server.pending or server.landed or server.inflight:
-        now = time.perf_counter()
-        while k < n_frames and t0 + k * period <= now:
-            server.submit(session, k, host_frames[k % ring], t0 + k * period)
-            k += 1
-        server.step()
+    was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        while k < n_frames or server.pending or server.landed or server.inflight:
+            now = time.perf_counter()
+            while k < n_frames and t0 + k * period <= now:
+                server.submit(session, k, host_frames[k % ring], t0 + k * period)
+                k += 1
+            server.step()
+    finally:
+        if was_enabled:
+            gc.enable()
 
 
 def latency_summary(lat: np.ndarray) -> dict:

@@ -45,3 +45,76 @@ def test_weighting_helps_at_high_counts(oracle_mod):
         es = np.sqrt(np.mean(((o["params"][c, 2] - tp[c, 2]) / tp[c, 2]) ** 2))
         res.append((ex, es))
     assert res[1][0] < 0.95 * res[0][0] and res[1][1] < 0.95 * res[0][1], res
+
+
+def _weighted_explicit_fit(model, W, H, g, w, v0):
+    """scipy's LM on the explicit weighted model: residuals sqrt(w_i) (alpha f_i + beta - g_i)."""
+    from scipy.optimize import least_squares
+    x = np.arange(W)[None, :]
+    y = np.arange(H)[:, None]
+    sw = np.sqrt(w)
+
+    def res(v):
+        if model == 0:
+            x0, y0, s, a, b = v
+            sx = sy = s
+        else:
+            x0, y0, sx, sy, a, b = v
+        f = np.exp(-0.5 * ((x - x0) / sx) ** 2 - 0.5 * ((y - y0) / sy) ** 2).ravel()
+        return sw * (a * f + b - g)
+
+    sol = least_squares(res, v0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
+    return sol.x, float((sol.fun ** 2).sum())
+
+
+def test_converged_weighted_fit_is_the_weighted_least_squares_minimum(oracle_mod):
+    """The weighted fit's fixed point equals the minimum of the weighted chi^2 over all 5 / 6
+    explicit unknowns (scipy), its amplitudes are the weighted least-squares solve at that
+    point, and its chi^2 is the weighted sum of squared residuals. Unit-weight and noise-free
+    checks cannot see a weight dropped from one term of the Jacobian; this one can, because
+    the weighted and unweighted minima of a noisy spot differ."""
+    rng = np.random.default_rng(77)
+    for model in (0, 1):
+        spots, dims, init, cases = [], [], [], []
+        for _ in range(12):
+            W, H = int(rng.integers(9, 25)), int(rng.integers(9, 25))
+            p = np.array([(W - 1) / 2 + rng.uniform(-1, 1), (H - 1) / 2 + rng.uniform(-1, 1),
+                          rng.uniform(1.2, 2.2), rng.uniform(1.2, 2.2)])
+            if model == 0:
+                p[3] = p[2]
+            xs, ys = np.arange(W)[None, :], np.arange(H)[:, None]
+            f = np.exp(-0.5 * ((xs - p[0]) / p[2]) ** 2 - 0.5 * ((ys - p[1]) / p[3]) ** 2).ravel()
+            g = rng.poisson(1200.0 * f + 60.0).astype(np.float64)
+            spots.append(g)
+            dims.append((W, H))
+            q = p + np.array([0.3, -0.2, 0.15, 0.15 if model else 0.15])
+            init.append(q)
+            cases.append((W, H, g))
+        offs = np.cumsum([0] + [s.size for s in spots[:-1]])
+        img = np.concatenate(spots)
+        init = np.array(init, np.float32)
+        o = oracle_mod.fit_spots_weighted(img, offs, dims, init, np.full(len(spots), model, np.uint8),
+                                          max_iter=200, min_delta=0.0, min_step=1e-13)
+        u = oracle_mod.fit_spots(img, offs, dims, init, np.full(len(spots), model, np.uint8),
+                                 max_iter=200, min_delta=0.0, min_step=1e-13)
+        P = 3 if model == 0 else 4
+        moved = 0.0
+        for s, (W, H, g) in enumerate(cases):
+            assert o["state"][s] in (1, 2, 4)
+            w = 1.0 / np.maximum(g, 1.0)
+            pw = o["params"][s]
+            xs, ys = np.arange(W)[None, :], np.arange(H)[:, None]
+            f = np.exp(-0.5 * ((xs - pw[0]) / pw[2]) ** 2 - 0.5 * ((ys - pw[1]) / pw[3]) ** 2).ravel()
+            sw = np.sqrt(w)
+            (a, b), *_ = np.linalg.lstsq(np.stack([sw * f, sw], 1), sw * g, rcond=None)
+            assert abs(a - o["alpha"][s]) <= 1e-9 * abs(a) and abs(b - o["beta"][s]) <= 1e-8 * abs(b)
+            chi = float((w * (g - a * f - b) ** 2).sum())
+            assert abs(chi - o["chi2"][s] * (W * H - P - 2)) <= 1e-10 * chi
+            v0 = list(pw[:P] + 0.05) + [0.9 * a, b + 3.0]
+            xv, chi_s = _weighted_explicit_fit(model, W, H, g, w, v0)
+            assert np.max(np.abs(xv[:P] - pw[:P])) < 1e-6
+            assert abs(xv[P] - a) < 1e-6 * abs(a)
+            assert chi <= chi_s * (1 + 1e-10)
+            moved = max(moved, float(np.max(np.abs(u["params"][s][:P] - pw[:P]))))
+        # the weights matter: the unweighted minimum lies elsewhere, far beyond the 1e-6 above
+        assert moved > 1e-3

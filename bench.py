@@ -617,8 +617,29 @@ def _e2e(args, b, out, ws, stream, barrier, world, dev):
     ms_max, conv_sum = job_totals(e2e_ms, conv_e2e, world, dev)
     e2e_value = conv_sum / (ms_max * 1e-3)
 
+    # the host link alone: one plain pinned host -> device copy of the same bytes, so that
+    # the line shows whether the end-to-end number is bound by the link or by the fits
+    d_img = torch.empty_like(b.images)
+    with torch.cuda.stream(stream):
+        d_img.copy_(h_img, non_blocking=True)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(2):
+            d_img.copy_(h_img, non_blocking=True)
+        c1.record(stream)
+    c1.synchronize()
+    copy_ms = c0.elapsed_time(c1) / 2
+    del d_img
+    img_bytes = h_img.numel() * h_img.element_size()
+    link = {"h2d_gbs": img_bytes / (copy_ms * 1e-3) / 1e9, "image_copy_ms": copy_ms,
+            "e2e_ms": e2e_ms,
+            "frac_of_link": copy_ms / e2e_ms,
+            "note": "one pinned copy of the images alone; frac_of_link near 1 = bound by the "
+                    "host link, not by the fits"}
+
     return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "chunk_spots": chunk, "call": "fit_spots_uniform_host (copies overlapped with fits)"}
+            "chunk_spots": chunk, "call": "fit_spots_uniform_host (copies overlapped with fits)",
+            "link": link}
 
 
 def main() -> None:

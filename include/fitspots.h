@@ -213,14 +213,16 @@ int fit_spots_backward(const void *images, int dtype, int64_t image_elems,
  * float [sessions][markers][4] = x, y, sigma_x, sigma_y, frame coordinates), clamped into
  * the frame, into rois[(b*markers + m) * roi*roi] (uint16), the warm start
  * init[b*markers + m] (ROI coordinates) and origin[b*markers + m] = (x, y) of the block.
- * roi must be 3..32 and fit in the frame. Entries b >= count are skipped.
+ * roi must be 3..32 and fit in the frame; markers and max_batch 1..65535 (else
+ * FS_ERR_ARG, nothing launched; FS_ERR_NULL for a NULL pointer). Entries b >= count are
+ * skipped. desc, state, rois, init and origin are caller-owned device memory.
  *
  * fs_serve_update: after fit_spots_uniform on the count*markers ROIs, move every marker
  * whose fit converged (state MIN_DELTA, MIN_STEP, MAX_ERROR or NO_DECREASE, finite
  * parameters) to origin + fitted centre (a lost marker keeps its last state), and write
  * results[b*markers + m][8] = (x, y, sigma_x, sigma_y in frame coordinates, alpha, beta,
  * normalised chi^2, fit state).
- * Both enqueue one kernel on stream and allocate nothing; the graph of a serving step is
+ * The same argument rules. Both enqueue one kernel on stream and allocate nothing; the graph of a serving step is
  * cut -> fit -> update. Not in the paper (it names the use, not a serving design).
  */
 int fs_serve_roi_cut(const uint16_t *frames, int frame_w, int frame_h, int roi, int markers,

@@ -122,7 +122,7 @@ int fs_serve_update(const int32_t *desc, int max_batch, int markers, const float
                     float *results, void *stream) {
   if (!desc || !params || !alpha || !beta || !chi2 || !fit_state || !origin || !state || !results)
     return FS_ERR_NULL;
-  if (markers < 1 || max_batch < 1) return FS_ERR_ARG;
+  if (markers < 1 || max_batch < 1 || markers > 65535 || max_batch > 65535) return FS_ERR_ARG;
   UpdArgs a{desc, markers, params, alpha, beta, chi2, fit_state, origin, state, results};
   const int total = markers * max_batch;
   state_update_kernel<<<(total + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a);

@@ -134,6 +134,29 @@ def test_start_and_explicit_argument_checks(lib):
         assert call(n=0) == 0 and call(images=None) == -1 and call(state=None) == -1
 
 
+def test_serving_argument_checks(lib):
+    """fs_serve_roi_cut and fs_serve_update reject NULL pointers and out-of-range sizes
+    before launching anything."""
+    from paper_2106_02045_gb300 import serving
+    serving._bind()
+    fake = ctypes.c_void_p(0x1000)
+
+    def cut(roi=21, fw=2048, fh=2048, markers=64, batch=8, frames=fake):
+        return lib.fs_serve_roi_cut(frames, fw, fh, roi, markers, fake, batch, fake, fake, fake,
+                                    fake, None)
+    assert cut(frames=None) == -1
+    assert cut(roi=2) == -8 and cut(roi=33) == -8 and cut(fw=20) == -8 and cut(fh=20) == -8
+    assert cut(markers=0) == -8 and cut(batch=0) == -8
+    assert cut(markers=65536) == -8 and cut(batch=65536) == -8
+
+    def upd(markers=64, batch=8, state=fake):
+        return lib.fs_serve_update(fake, batch, markers, fake, fake, fake, fake, fake, fake,
+                                   state, fake, None)
+    assert upd(state=None) == -1
+    assert upd(markers=0) == -8 and upd(batch=0) == -8
+    assert upd(markers=65536) == -8 and upd(batch=65536) == -8
+
+
 def test_size_classes_and_configs(lib):
     from paper_2106_02045_gb300 import fitspots
     assert lib.fit_spots_num_classes() == 16

@@ -592,7 +592,7 @@ def _e2e(args, b, out, ws, stream, barrier, world, dev):
     h_init = torch.empty(b.init.shape, dtype=b.init.dtype, pin_memory=True)
     h_init.copy_(b.init)
     h_out = fitspots.alloc_host_outputs(b.n)
-    chunk = E2E_CHUNK
+    chunk = args.e2e_chunk
     dtype = fitspots.U16 if b.images.dtype == torch.uint16 else fitspots.F32
     d_ws = torch.empty(fitspots.host_workspace_bytes(min(chunk, b.n), W, H, dtype),
                        dtype=torch.uint8, device=dev)
@@ -652,6 +652,8 @@ def main() -> None:
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunk", type=int, default=E2E_CHUNK,
+                    help="spots per chunk of the host-buffer call in the end-to-end leg")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
     ap.add_argument("--extras", default="mixed,backward,serving,start,table1,explicit,weighted",
                     help="comma-separated subset of mixed,backward,serving,start,table1,"

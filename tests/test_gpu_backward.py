@@ -86,6 +86,47 @@ def _oracle_errors(b, out, up):
     return errs, det
 
 
+def test_backward_full_size_iso16_sampled():
+    """All 262,144 iso16 spots, forward and backward in the launches the benchmark times;
+    the pixel gradients of a random sample of 512 spots against the oracle's FP64 backward
+    at its own polished fit."""
+    import oracle
+    b = synth.make_workload("iso16", None, device=DEV)
+    assert b.n == 262_144
+    fo = fitspots.fit_batch(b, **TIGHT)
+    gen = torch.Generator(device=DEV).manual_seed(7)
+    up = [torch.randn(b.n, 4, generator=gen, device=DEV)] + \
+         [torch.randn(b.n, generator=gen, device=DEV) for _ in range(3)]
+    grad = fitspots.backward(b.images, b.offsets, b.dims, b.model, fo, *up)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(b.n, 512, replace=False))
+    sub = b.subset(idx).to("cpu")
+    d = sub.numpy()
+    img = synth.as_numpy_images(sub)
+    ref = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"], max_iter=300,
+                           min_delta=0.0, min_step=1e-13)
+    offs = b.offsets.cpu().numpy()
+    grad = grad.cpu().numpy()
+    st = fo["state"].cpu().numpy()
+    ups = [u.cpu().numpy() for u in up]
+    errs = []
+    for j, s in enumerate(idx):
+        o = int(offs[s])
+        g_gpu = grad[o:o + 256].astype(np.float64)
+        gs = img[int(d["offsets"][j]):int(d["offsets"][j]) + 256].astype(np.float64)
+        u = np.concatenate([ups[0][s], [ups[1][s], ups[2][s], ups[3][s]]]).astype(np.float64)
+        ro = oracle.backward(0, 16, 16, gs, ref["params"][j], ref["alpha"][j], ref["beta"][j], u)
+        assert ro is not None
+        errs.append(np.linalg.norm(g_gpu - ro) / np.linalg.norm(ro))
+    errs = np.array(errs)
+    print(f"iso16 full-size backward sample: median {np.median(errs):.2e}, "
+          f"p99 {np.percentile(errs, 99):.2e}, max {errs.max():.2e}")
+    assert np.isin(st, fitspots.CONVERGED_STATES).mean() >= 0.999
+    assert np.mean(errs <= 1e-4) >= 0.99
+    assert np.median(errs) <= 1e-5
+
+
 def test_backward_matches_oracle_mixed_sizes():
     """Sizes 5..32 per side (row steps that do and do not divide the warp, odd heights,
     partial row groups) and both models: same per-spot bar as the 16x16 workload on the

@@ -78,6 +78,28 @@ def test_full_size_ell32_sampled():
     assert conv.mean() > 0.9
 
 
+def test_full_size_mixed_sampled():
+    """The 2,000,000-spot mixed workload (W, H in 5..32, both models, FP32) in the launch
+    the benchmark times (fit_spots: size-class prepass, one persistent launch per
+    configuration), checked on a random sample of spots the oracle fits one by one."""
+    b = synth.make_workload("mixed", None, device=DEV)
+    assert b.n == 2_000_000
+    out = fitspots.fit_batch(b)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(6)
+    idx = np.sort(rng.choice(b.n, 4000, replace=False))
+    sub = b.subset(idx).to("cpu")
+    ref = run_oracle(sub)
+    o = {k: v[torch.as_tensor(idx, device=DEV)].cpu().numpy() for k, v in out.items()}
+    m = compare(o, ref, sub.dims.numpy(), determined(sub, ref))
+    _report("mixed-full-sample", m)
+    assert m["n_well_posed"] >= 0.25 * idx.size
+    assert m["class_agree_wp"] >= 0.999 and m["bar_wp"] >= 0.999
+    assert m["class_agree"] >= 0.995 and m["bar_converged"] >= 0.97
+    st = out["state"].cpu().numpy()
+    assert np.isin(st, (1, 2, 3, 4)).mean() > 0.9 and not np.isin(st, (-2,)).any()
+
+
 def test_uniform_and_general_entry_points_agree_bitwise():
     for name in ("iso15", "ell32"):
         b = synth.make_workload(name, 3000, device=DEV)

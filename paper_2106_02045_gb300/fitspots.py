@@ -148,12 +148,13 @@ def fit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor, init: t
     _need(model, torch.uint8, "model", dev)
     if dims.numel() != 2 * n or init.numel() != 4 * n or model.numel() != n:
         raise FitSpotsError("offsets, dims, init and model disagree on the spot count")
-    o = out if out is not None else alloc_outputs(n, dev)
-    ws_need = workspace_bytes(n)
-    if workspace is None:
-        workspace = torch.empty(max(ws_need, 16), dtype=torch.uint8, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    with torch.cuda.device(dev):
+    # temporaries and outputs are allocated on the launch stream, so that the caching
+    # allocator never reuses their memory while the kernels may still run
+    with torch.cuda.device(dev), torch.cuda.stream(s):
+        o = out if out is not None else alloc_outputs(n, dev)
+        if workspace is None:
+            workspace = torch.empty(max(workspace_bytes(n), 16), dtype=torch.uint8, device=dev)
         rc = library().fit_spots(
             _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(init), _ptr(model),
             n, int(max_iter), float(max_error), float(min_delta), float(min_step),
@@ -184,12 +185,12 @@ def fit_uniform(images: torch.Tensor, width: int, height: int, model: int, init:
     n = init.numel() // 4
     if init.numel() != 4 * n or images.numel() < n * width * height:
         raise FitSpotsError("init must be [n, 4] and images must hold n*W*H elements")
-    o = out if out is not None else alloc_outputs(n, dev)
-    if workspace is None:
-        workspace = torch.empty(max(int(library().fit_spots_uniform_workspace()), 16),
-                                dtype=torch.uint8, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    with torch.cuda.device(dev):
+    with torch.cuda.device(dev), torch.cuda.stream(s):
+        o = out if out is not None else alloc_outputs(n, dev)
+        if workspace is None:
+            workspace = torch.empty(max(int(library().fit_spots_uniform_workspace()), 16),
+                                    dtype=torch.uint8, device=dev)
         rc = library().fit_spots_uniform(
             _ptr(images), dtype, int(width), int(height), int(model), _ptr(init), n,
             int(max_iter), float(max_error), float(min_delta), float(min_step),
@@ -240,10 +241,10 @@ def fit_uniform_host(images: torch.Tensor, width: int, height: int, model: int,
         if t is not None and t.device.type != "cpu":
             raise FitSpotsError(f"out[{k!r}] must be a host tensor")
     need = host_workspace_bytes(min(chunk, max(n, 1)), width, height, dtype)
-    if workspace is None:
-        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    with torch.cuda.device(dev):
+    with torch.cuda.device(dev), torch.cuda.stream(s):
+        if workspace is None:
+            workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
         rc = library().fit_spots_uniform_host(
             _ptr(images), dtype, int(width), int(height), int(model), _ptr(init), n,
             int(max_iter), float(max_error), float(min_delta), float(min_step),
@@ -271,9 +272,9 @@ def fit_explicit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor
     _need(init, torch.float32, "init", dev)
     _need(model, torch.uint8, "model", dev)
     n = offsets.numel()
-    o = out if out is not None else alloc_outputs(n, dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    with torch.cuda.device(dev):
+    with torch.cuda.device(dev), torch.cuda.stream(s):
+        o = out if out is not None else alloc_outputs(n, dev)
         rc = getattr(library(), _entry)(
             _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(init),
             _ptr(model), n, int(max_iter), float(max_error), float(min_delta), float(min_step),
@@ -309,10 +310,10 @@ def start_values(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor
     n = offsets.numel()
     if dims.numel() != 2 * n:
         raise FitSpotsError("dims must be [n, 2]")
-    o = out if out is not None else torch.empty((n, 4), dtype=torch.float32, device=dev)
-    _need(o, torch.float32, "out", dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    with torch.cuda.device(dev):
+    with torch.cuda.device(dev), torch.cuda.stream(s):
+        o = out if out is not None else torch.empty((n, 4), dtype=torch.float32, device=dev)
+        _need(o, torch.float32, "out", dev)
         rc = library().fit_spots_start(_ptr(images), dtype, images.numel(), _ptr(offsets),
                                        _ptr(dims), n, int(rule), _ptr(o),
                                        ctypes.c_void_p(s.cuda_stream))
@@ -364,10 +365,27 @@ def backward(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
              stream: torch.cuda.Stream | None = None) -> torch.Tensor:
     """d loss / d images for upstream gradients of a fit (implicit-function theorem)."""
     dev = images.device
-    dtype = U16 if images.dtype == torch.uint16 else F32
+    if dev.type != "cuda":
+        raise FitSpotsError("images must be a CUDA tensor")
+    dtype = U16 if images.dtype == torch.uint16 else F32 if images.dtype == torch.float32 else None
+    if dtype is None:
+        raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
+    _need(images, images.dtype, "images", dev)
+    _need(offsets, torch.int64, "offsets", dev)
+    _need(dims, torch.int32, "dims", dev)
+    _need(model, torch.uint8, "model", dev)
     n = int(offsets.numel())
-    if grad_images is None:
-        grad_images = torch.zeros(images.numel(), dtype=torch.float32, device=dev)
+    if dims.numel() != 2 * n or model.numel() != n:
+        raise FitSpotsError("offsets, dims and model disagree on the spot count")
+    for k, t, m in (("params", torch.float32, 4 * n), ("alpha", torch.float32, n),
+                    ("beta", torch.float32, n), ("state", torch.int32, n)):
+        _need(fit_out[k], t, f"fit_out[{k!r}]", dev)
+        if fit_out[k].numel() != m:
+            raise FitSpotsError(f"fit_out[{k!r}] has the wrong size")
+    if grad_images is not None:
+        _need(grad_images, torch.float32, "grad_images", dev)
+        if grad_images.numel() != images.numel():
+            raise FitSpotsError("grad_images must have as many elements as images")
 
     def opt(t, shape):
         if t is None:
@@ -376,10 +394,14 @@ def backward(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
         if t.numel() != shape:
             raise FitSpotsError("upstream gradient has the wrong size")
         return t
-    gp, ga = opt(grad_params, 4 * n), opt(grad_alpha, n)
-    gb, gc = opt(grad_beta, n), opt(grad_chi2, n)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    with torch.cuda.device(dev):
+    # conversions and the zeroed output are made on the launch stream: ordered before the
+    # kernel, and their memory is not reused while it runs
+    with torch.cuda.device(dev), torch.cuda.stream(s):
+        if grad_images is None:
+            grad_images = torch.zeros(images.numel(), dtype=torch.float32, device=dev)
+        gp, ga = opt(grad_params, 4 * n), opt(grad_alpha, n)
+        gb, gc = opt(grad_beta, n), opt(grad_chi2, n)
         rc = library().fit_spots_backward(
             _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(model), n,
             _ptr(fit_out["params"]), _ptr(fit_out["alpha"]), _ptr(fit_out["beta"]),

@@ -5,9 +5,11 @@ baseline leg of ``bench.py`` may import this package; the library itself never d
 The arithmetic lives in ``fitspots_oracle.c`` (plain C, double precision, one spot at a
 time, OpenMP across spots); this module compiles it with gcc and marshals numpy arrays.
 
-parity unpinned: the limit() box, the normalised chi^2 divisor, the maxError default
-and the NO_DECREASE / NOT_CONVERGED split are conventions read into the paper (see the
-header of ``fitspots_oracle.c``); nothing in the paper pins them.
+parity unpinned: the limit() box, the normalised chi^2 divisor, the maxError default and
+the damping schedule's constants are conventions or readings that no printed value pins
+(see the header of ``fitspots_oracle.c``). The NO_DECREASE exit and the order of the stop
+tests are pinned by the paper's stop-condition shares through a second build of the same
+source with the paper's FP32 chi^2 (``paper_arithmetic=True``).
 """
 from __future__ import annotations
 
@@ -21,30 +23,35 @@ import numpy as np
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "fitspots_oracle.c"
 _LIB = _HERE / "_build" / "liboracle.so"
+# the same source built with the paper's chi^2 arithmetic and minStep origin, for the pin
+# of the stop conditions the paper reports (see the header of fitspots_oracle.c)
+_LIB_PAPER = _HERE / "_build" / "liboracle_paper.so"
 
 MODEL_ISO, MODEL_ELLIPTIC = 0, 1
 U16, F32, F64 = 0, 1, 2
 STATE_NAMES = {0: "MAX_ITER", 1: "MIN_DELTA", 2: "MIN_STEP", 3: "MAX_ERROR",
                4: "NO_DECREASE", -1: "NOT_CONVERGED", -2: "INVALID"}
 
-_lib = None
+_libs = {}
 
 
-def build(force: bool = False) -> Path:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP)."""
-    _LIB.parent.mkdir(exist_ok=True)
-    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
-        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
-        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+def build(force: bool = False, paper_arithmetic: bool = False) -> Path:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP); with
+    ``paper_arithmetic`` the second build, ``liboracle_paper.so`` (-DOR_PAPER_ARITHMETIC)."""
+    lib_path = _LIB_PAPER if paper_arithmetic else _LIB
+    lib_path.parent.mkdir(exist_ok=True)
+    if force or not lib_path.exists() or lib_path.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = lib_path.with_suffix(f".{os.getpid()}.tmp")
+        defines = ["-DOR_PAPER_ARITHMETIC"] if paper_arithmetic else []
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", *defines,
                         "-o", str(tmp), str(_SRC), "-lm"], check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(str(build()))
+def _load(paper_arithmetic: bool = False):
+    if paper_arithmetic not in _libs:
+        lib = ctypes.CDLL(str(build(paper_arithmetic=paper_arithmetic)))
         d, i, i64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         lib.or_fit_spots.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
                                      vp, vp, vp, vp, vp, vp, vp, vp, i]
@@ -71,8 +78,8 @@ def _load():
         lib.or_profile_second.restype = None
         lib.or_backward.argtypes = [i, i, i, vp, vp, d, d, vp, vp]
         lib.or_backward.restype = i
-        _lib = lib
-    return _lib
+        _libs[paper_arithmetic] = lib
+    return _libs[paper_arithmetic]
 
 
 def _p(a: np.ndarray):
@@ -166,9 +173,11 @@ def limit(model: int, W: int, H: int, p):
 
 def fit_spots(images: np.ndarray, offsets, dims, init, model, *, max_iter: int = 20,
               max_error: float = 0.0, min_delta: float = 1e-6, min_step: float = 1e-4,
-              trace: bool = False, nthreads: int = 0) -> dict:
-    """Fit every spot in FP64. ``images`` is a flat uint16, float32 or float64 array."""
-    lib = _load()
+              trace: bool = False, nthreads: int = 0, paper_arithmetic: bool = False) -> dict:
+    """Fit every spot in FP64. ``images`` is a flat uint16, float32 or float64 array.
+    ``paper_arithmetic`` runs the second build (FP32 chi^2 over pixel threads, minStep
+    relative to the ROI centre), used only to pin the paper's stop-condition shares."""
+    lib = _load(paper_arithmetic)
     images = np.ascontiguousarray(images)
     dtype = {np.dtype(np.uint16): U16, np.dtype(np.float32): F32,
              np.dtype(np.float64): F64}[images.dtype]

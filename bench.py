@@ -14,7 +14,9 @@ than L2, so no flush is needed between steps). The JSON line reports:
                point (the separable evaluation: 1 FMA in the amplitude pass, 6 operations in
                the residual pass); direct_count repeats it with the work of a per-pixel
                implementation (12 per evaluated point plus 26 per gradient point)
-* cpu_baseline the FP64 oracle on the host cores, timed on a bounded sample of spots
+* cpu_baseline the FP64 oracle on the host cores, timed on a bounded sample of spots;
+               other_workloads adds the 15x15, 16x16 and mixed workloads (all cores) and
+               the 32x32 workload on one core
 
 ``--impl reference`` times the oracle itself as the reference arm (host cores only).
 Under torchrun every rank fits its own 1,000,000 spots (weak scaling, no collective on
@@ -165,6 +167,43 @@ def _cpu_baseline(batch_cpu, n_sample: int) -> dict:
                       f"{dt:.1f} s"}
 
 
+# the other workloads the oracle is timed on (all host cores), and the one-core sample
+CPU_DETAIL = (("iso15", 10_000), ("iso16", 50_000), ("mixed", 50_000))
+CPU_ONE_CORE_SAMPLE = 5_000
+
+
+def _cpu_baseline_detail(detail=CPU_DETAIL, one_core_sample: int = CPU_ONE_CORE_SAMPLE) -> dict:
+    """The FP64 oracle's converged fits/s on the other workloads (all host cores, each with
+    the tolerances its GPU section uses) and on the 32x32 workload with one core."""
+    import numpy as np
+    import oracle
+    from paper_2106_02045_gb300 import synth
+    cores = os.cpu_count() or 1
+
+    def timed(b, nthreads, **kw):
+        d = b.numpy()
+        img = synth.as_numpy_images(b)
+        t0 = time.perf_counter()
+        r = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"],
+                             nthreads=nthreads, **kw)
+        dt = time.perf_counter() - t0
+        return int(np.isin(r["state"], CONVERGED).sum()) / dt, dt
+
+    out = {}
+    for name, n in detail:
+        b = synth.make_workload(name, n, device="cpu")
+        kw = dict(max_iter=50, min_delta=0.0, min_step=1e-6) if name == "iso16" else {}
+        v, dt = timed(b, cores, **kw)
+        out[name] = {"value": v, "unit": UNIT, "cores": cores,
+                     "sample": f"{b.n:,} spots of the {name} workload, {dt:.2f} s"}
+    b = synth.make_workload(WORKLOAD, one_core_sample, device="cpu")
+    v, dt = timed(b, 1)
+    out[f"{WORKLOAD}_one_core"] = {"value": v, "unit": UNIT, "cores": 1,
+                                   "sample": f"{b.n:,} spots of the {WORKLOAD} workload, "
+                                             f"{dt:.2f} s"}
+    return out
+
+
 def run_reference(args) -> None:
     """The reference arm: the FP64 oracle on the host cores, same workload and metric."""
     world, rank, _ = _dist_env()
@@ -297,6 +336,7 @@ def run(args) -> None:
     if not args.no_cpu_baseline:
         bcpu = b.head(args.cpu_sample).to("cpu")
         cpu = _cpu_baseline(bcpu, args.cpu_sample)
+        cpu["other_workloads"] = _cpu_baseline_detail()
     extras = {} if args.no_extras else _extras(args, dev, set(args.extras.split(",")))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_job / args.steps,

@@ -42,3 +42,14 @@ def test_job_totals_two_gloo_ranks():
 def test_job_totals_single_rank_is_identity():
     import bench
     assert bench.job_totals(12.5, 42, 1, "cpu") == (12.5, 42.0)
+
+
+def test_cpu_baseline_detail_small():
+    """The oracle timings of the other workloads and of one core run on the host alone."""
+    import bench
+    out = bench._cpu_baseline_detail(detail=(("iso15", 200), ("iso16", 200), ("mixed", 300)),
+                                      one_core_sample=100)
+    assert set(out) == {"iso15", "iso16", "mixed", f"{bench.WORKLOAD}_one_core"}
+    for v in out.values():
+        assert v["value"] > 0 and v["unit"] == bench.UNIT and v["cores"] >= 1
+    assert out[f"{bench.WORKLOAD}_one_core"]["cores"] == 1

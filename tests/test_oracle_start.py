@@ -71,3 +71,49 @@ def test_matches_the_workload_generators():
     ref = synth.paper_start_values(p.images.reshape(p.n, -1), 9).numpy()
     out = st.start_values(p.images.numpy(), p.offsets.numpy(), p.dims.numpy(), st.PAPER)
     assert np.array_equal(out[:, :2], ref[:, :2])
+
+
+def _noisy_spot(rng, W, H):
+    ys, xs = np.mgrid[0:H, 0:W]
+    x, y = rng.uniform(3, W - 4), rng.uniform(3, H - 4)
+    s = rng.uniform(1.2, 2.5)
+    lam = 1500.0 * np.exp(-0.5 * ((xs - x) ** 2 + (ys - y) ** 2) / s**2) + 60.0
+    return rng.poisson(lam).astype(np.float64)
+
+
+def test_exact_invariances():
+    """Properties both rules have by definition, on integer-valued noisy spots (every FP32
+    decision exact): embedding the ROI in a larger one filled with its own minimum moves the
+    centre by the offset and leaves M alone (for the 3x3 rule when its best neighbourhood is
+    away from the border, where the clipped means change); a constant added to every pixel
+    leaves everything alone, a positive integer scale leaves the width (and the centroid)
+    alone; transposing the ROI swaps the centroid's x0 and y0 and keeps the width."""
+    rng = np.random.default_rng(21)
+    for _ in range(40):
+        W, H = int(rng.integers(9, 21)), int(rng.integers(9, 21))
+        g = _noisy_spot(rng, W, H)
+        for rule in (st.CENTROID, st.PAPER):
+            base = st.start_one(g.ravel(), W, H, rule)
+            # the extra pixels take the ROI's minimum: the centroid's weights (measured from
+            # the minimum) and M are unchanged; a lower fill would move the minimum
+            dx, dy = int(rng.integers(1, 32 - W + 1)), int(rng.integers(1, 32 - H + 1))
+            big = np.full((H + dy + 1, W + dx + 1), g.min())
+            big[dy:dy + H, dx:dx + W] = g.reshape(H, W)
+            emb = st.start_one(big.ravel(), W + dx + 1, H + dy + 1, rule)
+            if rule == st.CENTROID:
+                assert np.allclose(emb, base + [dx, dy, 0, 0], rtol=0, atol=1e-9)
+            else:
+                # the clipped border means of the small ROI are not those of the embedded
+                # one; the argmax agrees whenever it lies inside, away from the border
+                if 1 <= base[0] <= W - 2 and 1 <= base[1] <= H - 2:
+                    assert np.array_equal(emb, base + [dx, dy, 0, 0])
+            assert np.array_equal(st.start_one(g.ravel() + 250.0, W, H, rule), base)
+            assert np.array_equal(st.start_one(3.0 * g.ravel(), W, H, rule)[2:], base[2:])
+            if rule == st.CENTROID:
+                assert np.allclose(st.start_one(3.0 * g.ravel(), W, H, rule), base, atol=1e-9)
+            gt = g.reshape(H, W).T.ravel()
+            tr = st.start_one(gt, H, W, rule)
+            if rule == st.CENTROID:
+                assert np.allclose(tr, base[[1, 0, 2, 3]], atol=1e-9)
+            else:
+                assert tr[2] == base[2]

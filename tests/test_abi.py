@@ -134,6 +134,19 @@ def test_start_and_explicit_argument_checks(lib):
         assert call(n=0) == 0 and call(images=None) == -1 and call(state=None) == -1
 
 
+def test_backward_argument_checks(lib):
+    """fit_spots_backward rejects malformed calls before any CUDA call; n = 0 is a no-op."""
+    fake = ctypes.c_void_p(0x1000)
+
+    def call(n=10, dtype=1, elems=2560, images=fake, state=fake, grad=fake):
+        return lib.fit_spots_backward(images, dtype, elems, fake, fake, fake, n, fake, fake,
+                                      fake, state, None, None, None, None, grad, None)
+    assert call(n=-1) == -2 and call(n=2**31) == -2 and call(elems=-1) == -2
+    assert call(dtype=2) == -3 and call(dtype=-1) == -3
+    assert call(n=0) == 0
+    assert call(images=None) == -1 and call(state=None) == -1 and call(grad=None) == -1
+
+
 def test_serving_argument_checks(lib):
     """fs_serve_roi_cut and fs_serve_update reject NULL pointers and out-of-range sizes
     before launching anything."""

@@ -200,3 +200,14 @@ def test_binding_refuses_cpu_tensors():
     with pytest.raises(fitspots.FitSpotsError):
         fitspots.fit(x, torch.zeros(1, dtype=torch.int64), torch.zeros(1, 2, dtype=torch.int32),
                      torch.zeros(1, 4), torch.zeros(1, dtype=torch.uint8))
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the compiled library absent every call raises."""
+    from paper_2106_02045_gb300 import fitspots
+    monkeypatch.setattr(fitspots, "LIB", tmp_path / "missing.so")
+    monkeypatch.setattr(fitspots, "_lib", None)
+    with pytest.raises(fitspots.FitSpotsError, match="missing"):
+        fitspots.library()
+    with pytest.raises(fitspots.FitSpotsError):
+        fitspots.workspace_bytes(10)

@@ -6,7 +6,10 @@ e_x^T G e_y, and five row/column-weighted sums of the residual; the LM step asse
 alpha^, beta^ (Eq. 6), J^T r and J^T J (Eq. 12-14) from those. This test writes that
 assembly out in numpy (double precision, same sums and formulas as the kernel's LM step) and
 compares it with the oracle's explicit per-pixel normal equations, so an algebra slip in
-the reformulation would show here apart from any FP32 rounding."""
+the reformulation would show here apart from any FP32 rounding. The backward kernel's
+separable system (13 bilinear data sums, 1-D moments, the 6 x 6 system of the
+implicit-function theorem and its per-pixel gradient formula) is checked the same way
+against the oracle's backward."""
 import numpy as np
 import pytest
 
@@ -120,3 +123,103 @@ def test_separable_normal_equations_equal_the_per_pixel_form(oracle_mod, model):
         scale = np.sqrt(np.outer(np.diag(ref["A"]), np.diag(ref["A"])))
         assert np.max(np.abs(A - ref["A"]) / scale) < 1e-9
         assert np.max(np.abs(b - ref["b"]) / np.sqrt(np.diag(ref["A"]) * ref["chi2"])) < 1e-9
+
+
+def _backward_separable(g, W, H, p, al, beta, up, iso):
+    """The backward kernel's path in FP64: 13 data sums G_ab = sum g' e_x dx^a e_y dy^b, the
+    1-D moments, M over q = (x0, y0, sx, sy, alpha, beta) with the isotropic fold, M v = u,
+    then grad = e_x e_y (alpha (A(x) + B(y)) + v_alpha) + v_beta + c (g - alpha f - beta)."""
+    sh = float(np.rint(beta))
+    bp = beta - sh
+    sx, sy = p[2], (p[2] if iso else p[3])
+    ivx, ivy = 1 / sx**2, 1 / sy**2
+    cx, cy = ivx / sx, ivy / sy
+    dx = np.arange(W) - p[0]
+    dy = np.arange(H) - p[1]
+    ex = np.exp(-0.5 * dx**2 * ivx)
+    ey = np.exp(-0.5 * dy**2 * ivy)
+    Gp = g.reshape(H, W) - sh
+    G = {(a, b): (ex * dx**a) @ Gp.T @ (ey * dy**b)
+         for a, b in ((0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (3, 0), (2, 1), (1, 2),
+                      (0, 3), (4, 0), (2, 2), (0, 4))}
+    E = [(ex * dx**m).sum() for m in range(5)]
+    P = [(ex**2 * dx**m).sum() for m in range(5)]
+    F = [(ey * dy**m).sum() for m in range(5)]
+    Q = [(ey**2 * dy**m).sum() for m in range(5)]
+    N = W * H
+    DD = [ivx * ivx * P[2] * Q[0], ivx * ivy * P[1] * Q[1], ivx * cx * P[3] * Q[0],
+          ivx * cy * P[1] * Q[2], ivy * ivy * P[0] * Q[2], ivy * cx * P[2] * Q[1],
+          ivy * cy * P[0] * Q[3], cx * cx * P[4] * Q[0], cx * cy * P[2] * Q[2],
+          cy * cy * P[0] * Q[4]]
+    FD = [ivx * P[1] * Q[0], ivy * P[0] * Q[1], cx * P[2] * Q[0], cy * P[0] * Q[2]]
+    SD = [ivx * E[1] * F[0], ivy * E[0] * F[1], cx * E[2] * F[0], cy * E[0] * F[2]]
+    GD = [ivx * G[1, 0], ivy * G[0, 1], cx * G[2, 0], cy * G[0, 2]]
+    # sum g' h_jk, sum f h_jk, sum h_jk for the second derivatives h_jk of f / f
+    def hsum(s2):   # s2(a, b): the family's sum weighted by dx^a dy^b
+        return [ivx * ivx * s2(2, 0) - ivx * s2(0, 0), ivx * ivy * s2(1, 1),
+                ivx * cx * s2(3, 0) - 2 * cx * s2(1, 0), ivx * cy * s2(1, 2),
+                ivy * ivy * s2(0, 2) - ivy * s2(0, 0), ivy * cx * s2(2, 1),
+                ivy * cy * s2(0, 3) - 2 * cy * s2(0, 1),
+                cx * cx * s2(4, 0) - 3 * ivx * ivx * s2(2, 0), cx * cy * s2(2, 2),
+                cy * cy * s2(0, 4) - 3 * ivy * ivy * s2(0, 2)]
+    GH = hsum(lambda a, b: G[a, b])
+    FH = hsum(lambda a, b: P[a] * Q[b])
+    SH = hsum(lambda a, b: E[a] * F[b])
+    M = np.zeros((6, 6))
+    t = 0
+    for j in range(4):
+        for k in range(j, 4):
+            rh = GH[t] - al * FH[t] - bp * SH[t]
+            M[j, k] = M[k, j] = al * (al * DD[t] - rh)
+            t += 1
+    for j in range(4):
+        rd = GD[j] - al * FD[j] - bp * SD[j]
+        M[j, 4] = M[4, j] = al * FD[j] - rd
+        M[j, 5] = M[5, j] = al * SD[j]
+    M[4, 4], M[4, 5], M[5, 4], M[5, 5] = P[0] * Q[0], E[0] * F[0], E[0] * F[0], N
+    v = np.array(up[:6], dtype=np.float64)
+    if iso:
+        M[2, :] += M[3, :]
+        M[:, 2] += M[:, 3]
+        v[2] += v[3]
+        M[3, :] = 0
+        M[:, 3] = 0
+        M[3, 3] = 1
+        v[3] = 0
+    v = np.linalg.solve(M, v)
+    Ps = 3 if iso else 4
+    vx, vy, vsx, vsy = v[0] * ivx, v[1] * ivy, v[2] * cx, (v[2] if iso else v[3]) * cy
+    cchi = 2 * up[6] / (N - Ps - 2)
+    Ax = dx * (vx + vsx * dx)
+    By = dy * (vy + vsy * dy)
+    f = np.outer(ey, ex)
+    grad = f * (al * (Ax[None, :] + By[:, None]) + v[4]) + v[5] \
+        + cchi * (g.reshape(H, W) - al * f - beta)
+    return grad.ravel()
+
+
+@pytest.mark.parametrize("model", [ISO, ELL])
+def test_separable_backward_equals_the_oracle_ift(oracle_mod, model):
+    """The backward kernel's separable system and gradient formula, in FP64, against the
+    oracle's implicit-function-theorem VJP (explicit per-pixel K, second derivatives)."""
+    rng = np.random.default_rng(41 + model)
+    for _ in range(20):
+        W, H = int(rng.integers(5, 33)), int(rng.integers(5, 33))
+        truth = [(W - 1) / 2 + rng.uniform(-1, 1), (H - 1) / 2 + rng.uniform(-1, 1),
+                 rng.uniform(1.2, 2.5), rng.uniform(1.2, 2.5)]
+        sy_t = truth[2] if model == ISO else truth[3]
+        ys, xs = np.mgrid[0:H, 0:W]
+        lam = 1500 * np.exp(-0.5 * ((xs - truth[0]) / truth[2]) ** 2
+                            - 0.5 * ((ys - truth[1]) / sy_t) ** 2) + 90
+        g = rng.poisson(lam).astype(np.float64).ravel()
+        init = np.array([truth], np.float32)
+        if model == ISO:
+            init[0, 3] = init[0, 2]
+        o = oracle_mod.fit_spots(g, [0], [[W, H]], init, np.array([model], np.uint8),
+                                 max_iter=200, min_delta=0.0, min_step=1e-13)
+        p, al, be = o["params"][0], o["alpha"][0], o["beta"][0]
+        up = rng.standard_normal(7)
+        ref = oracle_mod.backward(model, W, H, g, p, al, be, up)
+        assert ref is not None
+        got = _backward_separable(g, W, H, p, al, be, up, model == ISO)
+        assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)

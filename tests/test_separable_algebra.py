@@ -223,3 +223,46 @@ def test_separable_backward_equals_the_oracle_ift(oracle_mod, model):
         assert ref is not None
         got = _backward_separable(g, W, H, p, al, be, up, model == ISO)
         assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("model", [ISO, ELL])
+def test_tie_refinement_equals_the_chi2_difference(oracle_mod, model):
+    """The kernels' refinement of a near-tie decision: with b the best point and t the trial,
+    h_t - h_b = f_b (alpha_t tt + alpha_t - alpha_b) + beta'_t - beta'_b, where
+    1 + tt = f_t / f_b = (1 + m_x)(1 + m_y) is formed from the exponent differences
+    m = expm1(d0 (dt + db) iv_t / 2 + db^2 (iv_b - iv_t) / 2) per axis, and
+    chi2_t - chi2_b = sum dh (dh - 2 r_b). Written out in FP64, it equals the difference of
+    the oracle's chi^2 at the two points."""
+    rng = np.random.default_rng(51 + model)
+    for _ in range(30):
+        W, H = int(rng.integers(5, 33)), int(rng.integers(5, 33))
+        truth = np.array([(W - 1) / 2 + rng.uniform(-1, 1), (H - 1) / 2 + rng.uniform(-1, 1),
+                          rng.uniform(1.2, 2.5), rng.uniform(1.2, 2.5)])
+        if model == ISO:
+            truth[3] = truth[2]
+        ys, xs = np.mgrid[0:H, 0:W]
+        lam = 1200 * np.exp(-0.5 * ((xs - truth[0]) / truth[2]) ** 2
+                            - 0.5 * ((ys - truth[1]) / truth[3]) ** 2) + 80
+        g = rng.poisson(lam).astype(np.float64).ravel()
+        pb = truth + rng.uniform(-0.05, 0.05, 4) * [1, 1, 0.2, 0.2]
+        pt = pb + rng.uniform(-1e-3, 1e-3, 4) * [1, 1, 0.1, 0.1]
+        if model == ISO:
+            pb[3], pt[3] = pb[2], pt[2]
+        eb, et = oracle_mod.evaluate(model, W, H, g, pb), oracle_mod.evaluate(model, W, H, g, pt)
+        ab, bb_, at, bt = eb["alpha"], eb["beta"], et["alpha"], et["beta"]
+
+        def mvec(n, c_t, c_b, s_t, s_b):
+            pos = np.arange(n, dtype=np.float64)
+            dt, db = pos - c_t, pos - c_b
+            ivt, ivb = 1 / s_t**2, 1 / s_b**2
+            return np.expm1(0.5 * ((c_t - c_b) * (dt + db) * ivt + db**2 * (ivb - ivt))), db, ivb
+        mx, dbx, ivbx = mvec(W, pt[0], pb[0], pt[2], pb[2])
+        my, dby, ivby = mvec(H, pt[1], pb[1], pt[3], pb[3])
+        exb, eyb = np.exp(-0.5 * dbx**2 * ivbx), np.exp(-0.5 * dby**2 * ivby)
+        fb = np.outer(eyb, exb)
+        tt = np.outer(my, 1 + mx) + mx[None, :]
+        dh = fb * (at * tt + (at - ab)) + (bt - bb_)
+        rb = g.reshape(H, W) - ab * fb - bb_
+        delta = (dh * (dh - 2 * rb)).sum()
+        exact = et["chi2"] - eb["chi2"]
+        assert abs(delta - exact) <= 1e-7 * abs(exact) + 1e-12 * eb["chi2"]

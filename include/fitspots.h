@@ -57,7 +57,7 @@ extern "C" {
 /* error codes */
 #define FS_OK 0
 #define FS_ERR_NULL (-1)       /* a required pointer is NULL                        */
-#define FS_ERR_SIZE (-2)       /* n < 0, n > 2^31-1 or image_elems < 0              */
+#define FS_ERR_SIZE (-2)       /* n < 0, n above the call's limit, image_elems < 0 */
 #define FS_ERR_DTYPE (-3)      /* unknown pixel type                                */
 #define FS_ERR_MAX_ITER (-4)   /* max_iter outside [1, 1000]                        */
 #define FS_ERR_TOL (-5)        /* a tolerance is negative or not finite, or          */
@@ -65,6 +65,17 @@ extern "C" {
 #define FS_ERR_WORKSPACE (-6)  /* workspace smaller than fit_spots_workspace(n)     */
 #define FS_ERR_CUDA (-7)       /* a CUDA call failed; see fit_spots_last_cuda_error  */
 #define FS_ERR_ARG (-8)        /* another argument is out of range                   */
+
+/*
+ * Largest spot count per call. The kernels hand out spots through 32-bit counters that
+ * run past the count by up to a few hundred thousand before every warp sees the end, so n
+ * stays 2^24 below 2^31. fit_spots_start, fit_spots_explicit and fit_spots_weighted return
+ * FS_ERR_SIZE above it; fit_spots, fit_spots_uniform, fit_spots_uniform_host and
+ * fit_spots_noalloc check only n <= 2^31 - 1 so far, and a caller must keep their n at or
+ * below FS_MAX_SPOTS too (the Python binding enforces it for every call). The backward
+ * pass accepts n <= 2^31 - 1.
+ */
+#define FS_MAX_SPOTS 2130706432LL   /* 2^31 - 2^24 */
 
 /* Bytes of device workspace that fit_spots needs for n spots (0 for n <= 0). The
  * workspace holds the spot schedule (size-class counts, cursors and a permutation of

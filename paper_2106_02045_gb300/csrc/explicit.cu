@@ -320,7 +320,7 @@ extern "C" int fit_spots_explicit(const void *images, int dtype, int64_t image_e
                                   double min_step, float *out_params, float *out_alpha,
                                   float *out_beta, float *out_chi2, int32_t *out_state,
                                   int32_t *out_iters, int32_t *out_evals, void *stream) {
-  if (n < 0 || n > INT32_MAX || image_elems < 0) return FS_ERR_SIZE;
+  if (n < 0 || n > FS_MAX_SPOTS || image_elems < 0) return FS_ERR_SIZE;
   if (dtype != FS_U16 && dtype != FS_F32) return FS_ERR_DTYPE;
   if (max_iter < 1 || max_iter > 1000) return FS_ERR_MAX_ITER;
   if (!(max_error >= 0.0) || !isfinite(max_error) || !(min_delta >= 0.0) || !(min_delta < 1.0) ||

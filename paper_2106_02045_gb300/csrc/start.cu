@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kStartThreads) start_kernel(StartArgs a) {
 extern "C" int fit_spots_start(const void *images, int dtype, int64_t image_elems,
                                const int64_t *offsets, const int32_t *roi_dims, int64_t n,
                                int rule, float *out_init, void *stream) {
-  if (n < 0 || n > INT32_MAX || image_elems < 0) return FS_ERR_SIZE;
+  if (n < 0 || n > FS_MAX_SPOTS || image_elems < 0) return FS_ERR_SIZE;
   if (dtype != FS_U16 && dtype != FS_F32) return FS_ERR_DTYPE;
   if (rule != FS_START_CENTROID && rule != FS_START_PAPER) return FS_ERR_ARG;
   if (n == 0) return FS_OK;

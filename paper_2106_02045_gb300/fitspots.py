@@ -18,10 +18,18 @@ U16, F32 = 0, 1
 STATE = {"MAX_ITER": 0, "MIN_DELTA": 1, "MIN_STEP": 2, "MAX_ERROR": 3, "NO_DECREASE": 4,
          "NOT_CONVERGED": -1, "INVALID_ROI": -2}
 CONVERGED_STATES = (1, 2, 3, 4)
+# largest spot count per call (FS_MAX_SPOTS of the C header: 2^31 - 2^24, headroom for the
+# kernels' 32-bit work counters)
+MAX_SPOTS = 2_130_706_432
 
 
 class FitSpotsError(RuntimeError):
     pass
+
+
+def _check_count(n: int) -> None:
+    if n > MAX_SPOTS:
+        raise FitSpotsError(f"{n} spots in one call; at most {MAX_SPOTS} (split the batch)")
 
 
 _lib = None
@@ -142,6 +150,7 @@ def fit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor, init: t
         raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
     _need(images, images.dtype, "images", dev)
     n = int(offsets.numel())
+    _check_count(n)
     _need(offsets, torch.int64, "offsets", dev)
     _need(dims, torch.int32, "dims", dev)
     _need(init, torch.float32, "init", dev)
@@ -183,6 +192,7 @@ def fit_uniform(images: torch.Tensor, width: int, height: int, model: int, init:
     _need(images, images.dtype, "images", dev)
     _need(init, torch.float32, "init", dev)
     n = init.numel() // 4
+    _check_count(n)
     if init.numel() != 4 * n or images.numel() < n * width * height:
         raise FitSpotsError("init must be [n, 4] and images must hold n*W*H elements")
     s = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -233,6 +243,7 @@ def fit_uniform_host(images: torch.Tensor, width: int, height: int, model: int,
     if init.dtype != torch.float32 or not init.is_contiguous() or not images.is_contiguous():
         raise FitSpotsError("images and init must be contiguous; init float32")
     n = init.numel() // 4
+    _check_count(n)
     if init.numel() != 4 * n or images.numel() < n * width * height:
         raise FitSpotsError("init must be [n, 4] and images must hold n*W*H elements")
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -272,6 +283,7 @@ def fit_explicit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor
     _need(init, torch.float32, "init", dev)
     _need(model, torch.uint8, "model", dev)
     n = offsets.numel()
+    _check_count(n)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     with torch.cuda.device(dev), torch.cuda.stream(s):
         o = out if out is not None else alloc_outputs(n, dev)
@@ -308,6 +320,7 @@ def start_values(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor
     _need(offsets, torch.int64, "offsets", dev)
     _need(dims, torch.int32, "dims", dev)
     n = offsets.numel()
+    _check_count(n)
     if dims.numel() != 2 * n:
         raise FitSpotsError("dims must be [n, 2]")
     s = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -375,6 +388,7 @@ def backward(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
     _need(dims, torch.int32, "dims", dev)
     _need(model, torch.uint8, "model", dev)
     n = int(offsets.numel())
+    _check_count(n)
     if dims.numel() != 2 * n or model.numel() != n:
         raise FitSpotsError("offsets, dims and model disagree on the spot count")
     for k, t, m in (("params", torch.float32, 4 * n), ("alpha", torch.float32, n),

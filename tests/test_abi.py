@@ -170,6 +170,25 @@ def test_serving_argument_checks(lib):
     assert upd(markers=65536) == -8 and upd(batch=65536) == -8
 
 
+def test_spot_count_limit(lib):
+    """FS_MAX_SPOTS (2^31 - 2^24) leaves the kernels' 32-bit work counters headroom: the
+    header's value is the binding's, and the calls that check it reject one spot more
+    before any CUDA work."""
+    from paper_2106_02045_gb300 import fitspots
+    text = (ROOT / "include" / "fitspots.h").read_text()
+    m = re.search(r"#define FS_MAX_SPOTS (\d+)LL", text)
+    assert m and int(m.group(1)) == fitspots.MAX_SPOTS == 2**31 - 2**24
+    over = fitspots.MAX_SPOTS + 1
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.fit_spots_start(fake, 0, 100, fake, fake, over, 0, fake, None) == -2
+    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted):
+        assert fn(fake, 0, 100, fake, fake, fake, fake, over, 20, 0.0, 1e-6, 1e-4,
+                  fake, fake, fake, fake, fake, fake, None, None) == -2
+    with pytest.raises(fitspots.FitSpotsError, match="at most"):
+        fitspots._check_count(over)
+    fitspots._check_count(fitspots.MAX_SPOTS)
+
+
 def test_size_classes_and_configs(lib):
     from paper_2106_02045_gb300 import fitspots
     assert lib.fit_spots_num_classes() == 16

@@ -53,3 +53,24 @@ def test_cpu_baseline_detail_small():
     for v in out.values():
         assert v["value"] > 0 and v["unit"] == bench.UNIT and v["cores"] >= 1
     assert out[f"{bench.WORKLOAD}_one_core"]["cores"] == 1
+
+
+def test_reference_arm_prints_one_json_line():
+    """``bench.py --impl reference`` (the oracle on the host cores) on a tiny sample: one
+    JSON line with the reference keys."""
+    import json
+    import subprocess
+    import sys
+    from pathlib import Path
+    root = Path(__file__).resolve().parents[1]
+    r = subprocess.run([sys.executable, str(root / "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1", "--ref-sample", "300"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "fits/s"
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]

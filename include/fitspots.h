@@ -292,7 +292,9 @@ int fit_spots_weighted(const void *images, int dtype, int64_t image_elems,
  * S_i / c_i > S_j / c_j as S_i c_j > S_j c_i, S summed row by row: each row's neighbours left
  * to right, then the rows top to bottom) are exact for integer-valued pixels below 2^21.
  * images/offsets/roi_dims as for fit_spots (W, H in 1..32); out_init device float[n][4]; an
- * invalid ROI gets four NaNs. Asynchronous on `stream`.
+ * invalid ROI gets four NaNs. Asynchronous on `stream`. Errors, before anything is
+ * enqueued: FS_ERR_SIZE (n < 0 or above FS_MAX_SPOTS, image_elems < 0), FS_ERR_DTYPE,
+ * FS_ERR_ARG (unknown rule), FS_ERR_NULL; n = 0 returns FS_OK without work.
  */
 #define FS_START_CENTROID 0
 #define FS_START_PAPER 1

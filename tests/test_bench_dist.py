@@ -74,3 +74,39 @@ def test_reference_arm_prints_one_json_line():
     assert d["higher_is_better"] is True and d["n_gpus"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_paper_protocol_section_with_a_stub(monkeypatch):
+    """The paper-protocol bench section's bookkeeping on the host, the library call replaced
+    by a stub that checks its arguments and marks every fit converged."""
+    import bench
+    import torch
+    from paper_2106_02045_gb300 import fitspots
+    calls = []
+
+    def fake_host(images, W, H, model, init, *, chunk, out, workspace, device, stream):
+        n = init.shape[0]
+        assert images.numel() == n * W * H and chunk == n and out["state"].shape[0] == n
+        assert workspace.numel() >= 256 and model == 0 and W == H
+        out["state"][:] = 1
+        calls.append((W, n))
+        return out
+
+    def fake_alloc(n):
+        return {k: torch.zeros(v, dtype=t) for k, (v, t) in dict(
+            params=((n, 4), torch.float32), alpha=(n, torch.float32), beta=(n, torch.float32),
+            chi2=(n, torch.float32), state=(n, torch.int32), iters=(n, torch.int32),
+            evals=(n, torch.int32)).items()}
+
+    class FakeStream:
+        def synchronize(self):
+            pass
+
+    monkeypatch.setattr(fitspots, "fit_uniform_host", fake_host)
+    monkeypatch.setattr(fitspots, "alloc_host_outputs", fake_alloc)
+    monkeypatch.setattr(bench, "PAPER_BATCHES", ((10, 3), (100, 2)))
+    monkeypatch.setattr(bench, "PAPER_SIZES", (9,))
+    out = bench._extra_paper_protocol("cpu", FakeStream(), pin=False)["paper_protocol"]
+    assert [(r["S"], r["batch"], r["calls"]) for r in out["rows"]] == [(9, 10, 3), (9, 100, 2)]
+    assert all(r["converged_fraction"] == 1.0 and r["fits_per_s"] > 0 for r in out["rows"])
+    assert calls == [(9, 10)] * 4 + [(9, 100)] * 3

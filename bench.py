@@ -327,12 +327,18 @@ def run(args) -> None:
         traffic *= n_spots / N_SPOTS
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "T lane-op/s", "frac": achieved / peak, "traffic": traffic,
+                "ops_definition": f"{OPS_PER_PIXEL_EVAL} FP32 ops (FMA = 1) per pixel per "
+                                  "evaluated point: the separable evaluation's unavoidable work",
                 "ops_per_launch": ops, "evals_per_spot": evals / n_spots,
                 # the same time against the work of a direct per-pixel evaluation: 12 ops per
                 # pixel per evaluated point and 26 more per pixel at each gradient point
                 # (one per LM iteration), elliptic model
                 "direct_count": {"iters_per_spot": iters / n_spots,
-                                 "frac": float(evals * 12 + iters * 26) * W * H / kernel_s / peak},
+                                 "frac": float(evals * 12 + iters * 26) * W * H / kernel_s / peak,
+                                 "ops_definition": "12 FP32 ops per pixel per evaluated point "
+                                                   "+ 26 per pixel per gradient point (one per "
+                                                   "LM iteration): a direct per-pixel "
+                                                   "evaluation's work, elliptic model"},
                 "peak_source": f"derived: {SMS} SMs x {LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz",
                 "kernel": _kernel_name(15)}
     cpu = None

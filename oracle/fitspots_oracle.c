@@ -144,6 +144,8 @@ int or_amplitudes(int N, const double *f, const double *g, double *alpha, double
 double or_chi2(int N, const double *f, const double *g, double alpha, double beta, double *r)
 {
 #ifdef OR_PAPER_ARITHMETIC
+    /* the second build (see the header): FP32 residuals, one per pixel thread, summed in
+     * FP32 by a pairwise tree as the paper's per-fit Sum over threads would */
     float t[OR_MAX_PIXELS];
     int m = 1;
     while (m < N) m <<= 1;

@@ -354,6 +354,44 @@ def test_symmetries(oracle_mod):
     assert abs(c[4] - 6.25 * c[0]) < 1e-7 * c[4]
 
 
+@pytest.mark.parametrize("model", [ISO, ELL])
+def test_symmetries_on_random_spots(oracle_mod, model):
+    """The same symmetries (transpose, both mirrors, offset, scale) on random sizes and
+    spots of both models, each variant fitted from the correspondingly moved start."""
+    rng = np.random.default_rng(60 + model)
+    for _ in range(8):
+        W, H = int(rng.integers(7, 33)), int(rng.integers(7, 33))
+        p = np.array([(W - 1) / 2 + rng.uniform(-1.5, 1.5), (H - 1) / 2 + rng.uniform(-1.5, 1.5),
+                      rng.uniform(1.2, 2.4), rng.uniform(1.2, 2.4)])
+        if model == ISO:
+            p[3] = p[2]
+        g = _spot(model, W, H, p, 1500, 70, rng).reshape(H, W)
+        s0 = np.array([p[0] + 0.3, p[1] - 0.2, p[2] * 1.1, p[3] * 0.9])
+        if model == ISO:
+            s0[3] = s0[2]
+        off = float(rng.integers(5, 200))
+        variants = [(g, (W, H), s0),
+                    (g.T.copy(), (H, W), s0[[1, 0, 3, 2]]),
+                    (g[:, ::-1].copy(), (W, H), [W - 1 - s0[0], s0[1], s0[2], s0[3]]),
+                    (g[::-1, :].copy(), (W, H), [s0[0], H - 1 - s0[1], s0[2], s0[3]]),
+                    (g + off, (W, H), s0), (g * 3.0, (W, H), s0)]
+        img, offs, dd = _pack([v[0].ravel() for v in variants], [v[1] for v in variants])
+        init = np.array([v[2] for v in variants], np.float32)
+        # min_step 1e-10: tight enough for the 1e-7 comparisons, loose enough that every fit
+        # ends on the step test rather than climbing to the damping cap at the FP64 floor
+        o = oracle_mod.fit_spots(img, offs, dd, init, np.full(6, model, np.uint8),
+                                 max_iter=300, min_delta=0.0, min_step=1e-10)
+        q, a, b = o["params"], o["alpha"], o["beta"]
+        assert np.isin(o["state"], (1, 2, 3, 4)).all()
+        tol = 1e-7
+        assert np.allclose(q[1], q[0][[1, 0, 3, 2]], atol=tol)
+        assert np.allclose(q[2], [W - 1 - q[0][0], q[0][1], q[0][2], q[0][3]], atol=tol)
+        assert np.allclose(q[3], [q[0][0], H - 1 - q[0][1], q[0][2], q[0][3]], atol=tol)
+        assert np.allclose(q[4], q[0], atol=tol) and abs(b[4] - b[0] - off) < 1e-6
+        assert np.allclose(q[5], q[0], atol=tol)
+        assert abs(a[5] - 3 * a[0]) < 1e-7 * a[5] and abs(a[4] - a[0]) < 1e-7 * a[0]
+
+
 def test_invalid_spots_are_flagged(oracle_mod):
     img = np.ones(4096, np.float32)
     offs = np.array([0, 100, 200, 300, 4000], np.int64)

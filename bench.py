@@ -9,11 +9,12 @@ than L2, so no flush is needed between steps). The JSON line reports:
                pinned host memory: the H2D copies of the step's pixels and start values and
                the D2H copies of all per-spot results are inside the timed region,
                overlapped with the fits chunk by chunk
-* roofline     the fit kernel against the FP32 lane-op peak (152 SMs x 128 lanes x max
-               clock), counting 7 algorithmic FP32 operations per pixel per evaluated
-               point (the separable evaluation: 1 FMA in the amplitude pass, 6 operations in
-               the residual pass); direct_count repeats it with the work of a per-pixel
-               implementation (12 per evaluated point plus 26 per gradient point)
+* roofline     the fit kernel against the FP32 FMA rate measured in this run
+               (fit_spots_probe_rates), counting the work of a per-pixel evaluation of the
+               method: 12 FP32 operations per pixel per evaluated point and 26 more per pixel
+               at each gradient point (elliptic model); `separable` repeats it with the 7
+               operations per pixel per evaluated point that the separable kernel cannot
+               avoid, `sfu` the exponentials against the measured MUFU rate
 * paper_protocol  the paper's own throughput protocol (batches of 10..10,000 9x9 and 32x32
                fits per call, host data to host results) through the host-buffer call, as
                context for the paper's printed fits/s
@@ -46,7 +47,8 @@ UNIT = "fits/s"
 WORKLOAD = "ell32"
 W = H = 32
 N_SPOTS = 1_000_000
-OPS_PER_PIXEL_EVAL = 7          # algorithmic FP32 ops per pixel per evaluated point
+OPS_PER_PIXEL_EVAL = 7          # separable kernel: FP32 ops per pixel per evaluated point
+C_V, C_D = 12, 26               # per-pixel evaluation (elliptic): per point, per gradient point
 SMS, LANES_PER_SM = 152, 128
 CONVERGED = (1, 2, 3, 4)
 PROFILE = ROOT / "profiles" / "fit_kernel_ell32.md"
@@ -258,6 +260,8 @@ def run(args) -> None:
     __graft_entry__.build()
     from paper_2106_02045_gb300 import fitspots, synth
 
+    # roofline denominators, measured on this GPU before the timed region
+    rates = fitspots.probe_rates(dev)
     n_spots = args.spots
     b = synth.make_workload(WORKLOAD, n_spots, device=dev)
     if rank > 0:   # each rank its own draw of the workload
@@ -313,33 +317,31 @@ def run(args) -> None:
         return
     # ---------------------------------------------------------------- roofline
     kernel_s = statistics.mean(kernel_ms) * 1e-3
-    ops = float(evals) * W * H * OPS_PER_PIXEL_EVAL
-    peak_mhz = 2070.0
-    try:
-        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
-        peak_mhz = float(peaks.get("sm_max_mhz", peak_mhz))
-    except (OSError, ValueError):
-        pass
-    peak = SMS * LANES_PER_SM * peak_mhz * 1e6
-    achieved = ops / kernel_s
+    peak = rates["ffma"]
+    ops_direct = float(evals * C_V + iters * C_D) * W * H
+    ops_sep = float(evals) * W * H * OPS_PER_PIXEL_EVAL
+    exps_sep = float(evals) * (W + H)
     traffic = _traffic_from_profile()
     if traffic is not None:
         traffic *= n_spots / N_SPOTS
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "T lane-op/s", "frac": achieved / peak, "traffic": traffic,
-                "ops_definition": f"{OPS_PER_PIXEL_EVAL} FP32 ops (FMA = 1) per pixel per "
-                                  "evaluated point: the separable evaluation's unavoidable work",
-                "ops_per_launch": ops, "evals_per_spot": evals / n_spots,
-                # the same time against the work of a direct per-pixel evaluation: 12 ops per
-                # pixel per evaluated point and 26 more per pixel at each gradient point
-                # (one per LM iteration), elliptic model
-                "direct_count": {"iters_per_spot": iters / n_spots,
-                                 "frac": float(evals * 12 + iters * 26) * W * H / kernel_s / peak,
-                                 "ops_definition": "12 FP32 ops per pixel per evaluated point "
-                                                   "+ 26 per pixel per gradient point (one per "
-                                                   "LM iteration): a direct per-pixel "
-                                                   "evaluation's work, elliptic model"},
-                "peak_source": f"derived: {SMS} SMs x {LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz",
+    roofline = {"bound": "alu", "achieved": ops_direct / kernel_s / 1e12, "peak": peak / 1e12,
+                "unit": "T lane-op/s", "frac": ops_direct / kernel_s / peak, "traffic": traffic,
+                "ops_definition": f"{C_V} FP32 ops (FMA = 1) per pixel per evaluated point + "
+                                  f"{C_D} per pixel per gradient point (one per LM iteration): "
+                                  "the work of a per-pixel evaluation of the method, elliptic",
+                "ops_per_launch": ops_direct, "evals_per_spot": evals / n_spots,
+                "iters_per_spot": iters / n_spots,
+                "peak_source": "measured in this run: FP32 FMA chains on every SM "
+                               "(fit_spots_probe_rates), 'of measured'",
+                "separable": {"frac": ops_sep / kernel_s / peak,
+                              "achieved": ops_sep / kernel_s / 1e12,
+                              "ops_definition": f"{OPS_PER_PIXEL_EVAL} FP32 ops per pixel per "
+                                                "evaluated point: the separable evaluation's "
+                                                "unavoidable work"},
+                "sfu": {"frac": exps_sep / kernel_s / rates["ex2"],
+                        "achieved": exps_sep / kernel_s / 1e12, "peak": rates["ex2"] / 1e12,
+                        "ops_definition": "W + H exponentials per evaluated point (separable)"},
+                "fp64_peak": rates["dfma"] / 1e12,
                 "kernel": _kernel_name(15)}
     cpu = None
     if not args.no_cpu_baseline:
@@ -579,6 +581,7 @@ def _extra_start(dev, stream, hbm) -> dict:
 def _extra_mixed(args, dev, stream) -> dict:
     import torch
     from paper_2106_02045_gb300 import fitspots, synth
+    from paper_2106_02045_gb300.autotune import class_of as autotune_class
     out = {}
     # mixed sizes 5..32, both models, 2,000,000 spots (fit_spots with the size-class prepass)
     mb = synth.make_workload("mixed", args.mixed_spots, device=dev)
@@ -588,30 +591,29 @@ def _extra_mixed(args, dev, stream) -> dict:
     conv = int(torch.isin(mo["state"], torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())
     out["mixed"] = {"workload": f"mixed: {mb.n:,} spots, W,H ~ U{{5..32}}, models 50/50, FP32",
                     "value": conv / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                    "launches_per_step": "memset + 3 prepass + one persistent launch per "
-                                         "configuration in use"}
-    # the plain alternative: one fit_spots_uniform launch per (W, H, model), the spots of
-    # each size stored back to back (the layout of the paper's kernel; the regrouping
-    # copies are not timed), launched one after another on the stream
-    key = (mb.dims[:, 0].to(torch.int64) * 64 + mb.dims[:, 1]) * 2 + mb.model.to(torch.int64)
-    groups = []
-    uws = torch.empty(max(fitspots.uniform_workspace_bytes(), 16), dtype=torch.uint8, device=dev)
-    for k in torch.unique(key).tolist():
-        idx = torch.nonzero(key == k).flatten()
-        gw, gh, gm = int(k // 2 // 64), int(k // 2 % 64), int(k % 2)
-        cols = mb.offsets[idx][:, None] + torch.arange(gw * gh, device=dev)[None, :]
-        groups.append((mb.images[cols.reshape(-1)].contiguous(), gw, gh, gm,
-                       mb.init[idx].contiguous(), fitspots.alloc_outputs(idx.numel(), dev)))
-
-    def per_size():
-        for imgs, gw, gh, gm, ini, o in groups:
-            fitspots.fit_uniform(imgs, gw, gh, gm, ini, out=o, workspace=uws, stream=stream)
-    pms = _timed(per_size, 3, stream)
-    out["mixed"]["one_launch_per_size"] = {
-        "ms_per_step": pms, "launches_per_step": len(groups),
-        "persistent_speedup": pms / ms,
-        "what": "one fit_spots_uniform launch per distinct (W, H, model), sizes back to back"}
-    del groups
+                    "fit_launches_per_step": 1,
+                    "launches_per_step": "memset + 3 prepass kernels + one persistent fit launch "
+                                         "for all size classes"}
+    # the plain form: the same prepass, then one persistent launch per size class in use
+    pcs = _timed(lambda: fitspots.fit_batch(mb, out=mo, workspace=mws, stream=stream,
+                                            per_class=True), 3, stream)
+    used = int(torch.unique(torch.tensor([autotune_class(int(w), int(h)) for w, h in
+                                          torch.unique(mb.dims, dim=0).tolist()])).numel())
+    out["mixed"]["one_launch_per_class"] = {
+        "ms_per_step": pcs, "fit_launches_per_step": used, "single_launch_speedup": pcs / ms,
+        "what": "fit_spots_per_class: the same prepass and kernels, one persistent launch per "
+                "size class in use"}
+    # elongated ROIs (a side above 32, at most 1024 pixels) through the same single launch
+    eb = synth.make_workload("elongated", None, device=dev)
+    eo = fitspots.alloc_outputs(eb.n, dev)
+    ews = torch.empty(fitspots.workspace_bytes(eb.n), dtype=torch.uint8, device=dev)
+    ems = _timed(lambda: fitspots.fit_batch(eb, out=eo, workspace=ews, stream=stream), 3, stream)
+    econv = int(torch.isin(eo["state"], torch.tensor(CONVERGED, device=dev, dtype=torch.int32)).sum())
+    out["elongated"] = {"workload": f"elongated: {eb.n:,} spots, 64x16 .. 341x3 and transposes, "
+                                    "both models, FP32", "value": econv / (ems * 1e-3),
+                        "unit": UNIT, "ms_per_step": ems,
+                        "converged_fraction": econv / eb.n}
+    del eb, eo, ews
     # autotuned: every usable configuration timed per size class on a 4,096-spot sample
     from paper_2106_02045_gb300 import autotune
     t0 = time.perf_counter()

@@ -52,7 +52,7 @@ extern "C" {
 #define FS_STATE_MAX_ERROR 3       /* converged: chi^2 < max_error                      */
 #define FS_STATE_NO_DECREASE 4     /* converged: step below min_step without decrease   */
 #define FS_STATE_NOT_CONVERGED (-1)/* NaN, singular system, or damping reached 10^4     */
-#define FS_STATE_INVALID_ROI (-2)  /* W or H outside 3..32, W*H<=P+2, bad model/offset */
+#define FS_STATE_INVALID_ROI (-2)  /* W or H < 3, W*H > 1024 or <= P+2, bad model/offset */
 
 /* error codes */
 #define FS_OK 0
@@ -69,20 +69,17 @@ extern "C" {
 /*
  * Largest spot count per call. The kernels hand out spots through 32-bit counters that
  * run past the count by up to a few hundred thousand before every warp sees the end, so n
- * stays 2^24 below 2^31. fit_spots_start, fit_spots_explicit and fit_spots_weighted return
- * FS_ERR_SIZE above it; fit_spots, fit_spots_uniform, fit_spots_uniform_host and
- * fit_spots_noalloc check only n <= 2^31 - 1 so far, and a caller must keep their n at or
- * below FS_MAX_SPOTS too (the Python binding enforces it for every call). The backward
- * pass accepts n <= 2^31 - 1.
+ * stays 2^24 below 2^31. Every entry point that takes a spot count returns FS_ERR_SIZE
+ * above it, before anything is enqueued.
  */
 #define FS_MAX_SPOTS 2130706432LL   /* 2^31 - 2^24 */
 
-/* Bytes of device workspace that fit_spots needs for n spots (0 for n <= 0). The
- * workspace holds the spot schedule (size-class counts, cursors and a permutation of
- * the spot indices); its contents on entry do not matter. */
+/* Bytes of device workspace that fit_spots needs for n spots (0 for n <= 0):
+ * 272 + 4 n. The workspace holds the spot schedule (counts, starts and cursors of the 17
+ * size classes and a permutation of the spot indices); its contents on entry do not matter. */
 size_t fit_spots_workspace(int64_t n);
 
-/* Bytes of device workspace that fit_spots_uniform needs (independent of n). */
+/* Bytes of device workspace that fit_spots_uniform needs (272, independent of n). */
 size_t fit_spots_uniform_workspace(void);
 
 /*
@@ -90,8 +87,9 @@ size_t fit_spots_uniform_workspace(void);
  *   images       device, uint16 (FS_U16) or float32 (FS_F32) pixel buffer
  *   image_elems  number of elements in `images`; spots reaching past it are INVALID
  *   offsets      device int64[n], element offset of each spot
- *   roi_dims     device int32[n][2] = (W, H), each in 3..32: at most 1024 pixels per
- *                spot, the bound of Sec. "Implementation"
+ *   roi_dims     device int32[n][2] = (W, H), each at least 3, W * H at most 1024 pixels
+ *                (the bound of Sec. "Implementation"), so the longer side is at most 341;
+ *                ROIs with a side above 32 form the elongated size class
  *   init_params  device float[n][4], start parameters; clamped by limit() first
  *   model        device uint8[n], FS_MODEL_*
  *   max_iter     iteration budget, 1..1000 (the paper's benchmark uses 20)
@@ -109,6 +107,9 @@ size_t fit_spots_uniform_workspace(void);
  * Invalid spots get their start parameters back, NaN amplitudes and chi^2, 0 iterations.
  * Results of a spot depend only on that spot's inputs and the size-class configuration
  * in force (fit_spots_set_config), never on the other spots of the batch.
+ * Launches: a prepass (three small kernels) sorts the spots by size class, then one
+ * persistent launch of the generic configuration fits every class (each ROI oriented with
+ * its longer side along the lanes when that side is at most 32, rows in blocks of 32).
  */
 int fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
               const int32_t *roi_dims, const float *init_params, const uint8_t *model,
@@ -118,10 +119,26 @@ int fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t 
               size_t ws_bytes, void *stream);
 
 /*
+ * fit_spots with one persistent launch per size class in use (the prepass, then each class
+ * alone, largest first, with the configuration fit_spots_set_config assigns to it) instead of
+ * one launch of the generic configuration for all classes. Same arguments and workspace; the
+ * results agree with fit_spots to FP32 rounding (bit for bit where the class's configuration
+ * is the generic one). The plain form that the single launch is compared with.
+ */
+int fit_spots_per_class(const void *images, int dtype, int64_t image_elems,
+                        const int64_t *offsets, const int32_t *roi_dims,
+                        const float *init_params, const uint8_t *model, int64_t n, int max_iter,
+                        double max_error, double min_delta, double min_step, float *out_params,
+                        float *out_alpha, float *out_beta, float *out_chi2, int32_t *out_state,
+                        int32_t *out_iters, int32_t *out_evals, void *workspace,
+                        size_t ws_bytes, void *stream);
+
+/*
  * Fit n spots of one size and model stored back to back, the layout of the paper's
  * Fit2DGaussian kernel (one width and pixel count per launch): spot s occupies elements
  * [s*W*H, (s+1)*W*H) of `images`. One kernel launch, no prepass.
- *   width, height  W and H, each in 3..32 (FS_ERR_ARG otherwise, or if W*H <= P + 2)
+ *   width, height  W and H, each at least 3 with W*H <= 1024 (FS_ERR_ARG otherwise, or if
+ *                  W*H <= P + 2)
  *   model_id       FS_MODEL_ISO or FS_MODEL_ELLIPTIC for every spot
  *   workspace      device scratch of at least fit_spots_uniform_workspace() bytes,
  *                  16-byte aligned (the work cursor)
@@ -167,11 +184,13 @@ int fit_spots_uniform_host(const void *images, int dtype, int width, int height,
  * whose host application owns every allocation) or that has no allocator of its own at
  * hand. The paper has no counterpart; this is a convenience of the library.
  * The schedule scratch is a fixed array compiled into the library, sized for
- * fit_spots_noalloc_max_spots() = 1,048,576 spots (4 MiB + 256 B), which every GPU that
+ * fit_spots_noalloc_max_spots() = 1,048,576 spots (4 MiB + 272 B), which every GPU that
  * loads the library holds until the process exits. n above that limit returns
  * FS_ERR_SIZE. The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call before any
- * stream capture. The call itself allocates nothing and frees nothing. Every call shares
+ * stream capture; later calls outside a capture look it up again (so a device reset does
+ * not leave a stale address behind), calls inside one reuse the last address. The call
+ * itself allocates nothing and frees nothing. Every call shares
  * the one array and leaves its schedule in it: calls that may overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. Each call
  * clears the parts that must start at zero, so results never depend on an earlier call.
@@ -303,15 +322,21 @@ int fit_spots_start(const void *images, int dtype, int64_t image_elems, const in
 
 /*
  * Size classes and their kernel configurations.
- * A spot's size class is (ceil(W/8)-1)*4 + (ceil(H/8)-1), i.e. 16 classes for W, H in
- * 3..32. Each class runs one kernel configuration: `lanes` threads per spot (4, 8, 16
- * or 32), `cols` ROI columns held by each thread (lanes*cols covers the class's width
- * bound and stays below the next one), and the class's row bound (8, 16, 24 or 32) as
- * the per-thread row count. A configuration is per-spot (each lane group fits one spot
- * from start to stop, every lane running the LM step) or batched
+ * A spot with W, H <= 32 has size class (ceil(W/8)-1)*4 + (ceil(H/8)-1) (classes 0..15);
+ * a spot with a side above 32 (W*H <= 1024) is in class 16, the elongated class. Each class
+ * runs one kernel configuration: `lanes` threads per spot (4, 8, 16 or 32), `cols` ROI
+ * columns held by each thread (lanes*cols covers the class's width bound), and the class's
+ * row bound (8, 16, 24 or 32) as the per-thread row count. A configuration is per-spot (each
+ * lane group fits one spot from start to stop, every lane running the LM step) or batched
  * (fit_spots_config_batched = 1): a warp keeps 16 spots in flight, its lane groups evaluate
  * them with that geometry, re-reading the pixels at each evaluation, and lane j runs the LM
  * step of spot j; per-spot and batched results of the same geometry agree to FP32 rounding.
+ * The generic configuration (32 lanes, 1 column, 32 rows, up to 11 row blocks) takes any ROI
+ * of at most 1024 pixels: each ROI is oriented with its longer side along the lanes when that
+ * side is at most 32, else with its shorter side there, and its rows are walked in blocks of
+ * 32 (an oriented ROI may be the caller's transpose; the parameters come back in the caller's
+ * orientation). It is the only configuration of the elongated class and the one fit_spots
+ * launches once for a whole mixed batch.
  * fit_spots_num_configs / fit_spots_config_info
  * enumerate the compiled configurations; fit_spots_set_config assigns one to a class
  * (the autotuner's output) and fails with FS_ERR_ARG if it cannot hold the class.
@@ -321,9 +346,26 @@ int fit_spots_num_configs(void);
 int fit_spots_config_info(int config, int *lanes, int *cols, int *rows);
 int fit_spots_config_batched(int config); /* 1 batched, 0 per-spot, FS_ERR_ARG if unknown */
 int fit_spots_config_fits(int size_class, int config); /* 1 if usable, else 0 */
+/* 1 if `config` is the generic configuration (the one fit_spots launches once for all size
+ * classes, and the only one that serves the elongated class), 0 otherwise, FS_ERR_ARG if
+ * unknown */
+int fit_spots_config_generic(int config);
 int fit_spots_get_config(int size_class);
 int fit_spots_default_config(int size_class); /* the built-in choice the library starts with */
 int fit_spots_set_config(int size_class, int config);
+
+/*
+ * Throughput probes for the roofline of the fits (not in the paper; measurement support).
+ * fit_spots_probe_rates runs dependency chains of FP32 FMA, MUFU exp2 and FP64 FMA on `sms`
+ * x 8 blocks of 256 threads, times each with CUDA events on `stream` (one warm-up launch
+ * first) and writes lane-operations per second to *ffma, *ex2 and *dfma. It synchronises
+ * on its events. scratch: device memory of at least fit_spots_probe_scratch_bytes(sms)
+ * bytes (the chains' results are written there). Returns FS_OK, FS_ERR_NULL, FS_ERR_ARG
+ * (sms outside 1..4096), FS_ERR_WORKSPACE or FS_ERR_CUDA.
+ */
+size_t fit_spots_probe_scratch_bytes(int sms);
+int fit_spots_probe_rates(int sms, void *scratch, size_t scratch_bytes, double *ffma, double *ex2,
+                          double *dfma, void *stream);
 
 #ifdef __cplusplus
 }

@@ -38,7 +38,9 @@
  *   R11 lambda = 10^k with integer k, k = -2 at the start of each fit; "lambda < 10^4"
  *       is k < 4 (exactly the paper's schedule, free of rounding in the comparison).
  *   R12 the elliptic (axis-aligned) model, parameters (x, y, sigma_x, sigma_y).
- *   R13 a ROI is at most 32 x 32 pixels (the paper bounds the pixel count by 1024).
+ *   R13 a ROI has at most 1024 pixels (the paper's bound on the pixels of one fit) and
+ *       both sides at least 3, so the longer side is at most 341; the explicit and weighted
+ *       comparison fits keep both sides at most 32.
  * Pixel i of a W x H spot sits at x_i = i mod W, y_i = floor(i / W) (row-major).
  *
  * parity unpinned: limit() bounds (R8), normalised chi^2 (R9) and the maxError default
@@ -70,7 +72,7 @@
 #endif
 
 #define OR_MAX_PIXELS 1024
-#define OR_MAX_SIDE 32 /* R13: W, H <= 32, so W*H <= 1024 (Sec. "Implementation") */
+#define OR_MAX_SIDE 32 /* sides of the explicit and weighted comparison fits */
 
 /* spot models */
 #define OR_MODEL_ISO 0
@@ -323,70 +325,120 @@ static int all_small(int P, int W, int H, const double *delta, const double *bes
     return 1;
 }
 
-/* One spot: the damped LM loop of Sec. "Levenberg-Marquardt algorithm" with the stop
- * criteria of the Fit2DGaussian listing. p0 is the caller's start point (4 values; the
- * isotropic model uses p0[2] as sigma). Outputs p (4 values; isotropic writes sigma
- * into both slots 2 and 3), alpha^, beta^, normalised chi^2, outcome, iterations and the
- * number of evaluated points. trace (max_iter + 1 values, or NULL) receives the error at
- * the start of every iteration followed by the final error; unused slots are NaN. */
+/* A point of the search: parameters, the amplitudes of Eq. 6 there and the error of Eq. 2. */
+typedef struct {
+    double p[4], alpha, beta, chi2;
+} or_point;
+
+/* One spot under fit: model, size, data, the shape-parameter count and the tolerances. */
+typedef struct {
+    int model, W, H, P;
+    const double *g;
+    double max_error, min_delta, min_step;
+} or_spot;
+
+/* Outcomes of the damping search of one iteration. */
+#define OR_SEARCH_DECREASED 0 /* a trial point lowered (or kept) the error          */
+#define OR_SEARCH_STALLED 1   /* the step fell below minStep without a decrease     */
+#define OR_SEARCH_FAILED 2    /* no solvable damped system, a NaN, or damping 10^4  */
+/* Stop-test result meaning "take another iteration". */
+#define OR_CONTINUE 100
+
+/* One damped step from `from` (Eq. 14 with lambda = 10^k) and its trial point
+ * limit(from + delta) with amplitudes and error (Eq. 6, Eq. 2). Returns -1 when the damped
+ * normal matrix is not positive definite, else 0 (the trial error may be NaN). */
+static int damped_trial(const or_spot *sp, double A[4][4], const double *b, int k,
+                        const or_point *from, double *delta, or_point *to, int *evals)
+{
+    if (solve_damped(sp->P, A, b, pow(10.0, k), delta)) return -1;
+    ++*evals;
+    to->chi2 = trial(sp->model, sp->W, sp->H, sp->g, from->p, delta, to->p, &to->alpha,
+                     &to->beta);
+    return 0;
+}
+
+/* The damping search of one iteration (Sec. "Levenberg-Marquardt algorithm"): the first
+ * trial uses the damping carried over from the last iteration, and a decrease there relaxes
+ * the damping tenfold for the next one; while the trial error exceeds the current error, the
+ * step is not yet below minStep and lambda < 10^4, the damping grows tenfold and the step is
+ * solved again from the same normal equations (readings R3, R11). An equal error counts as a
+ * decrease (R10). The last step is left in delta and the last trial point in `next`. */
+static int damping_search(const or_spot *sp, double A[4][4], const double *b, int *k,
+                          const or_point *cur, or_point *next, double *delta, int *evals)
+{
+    if (damped_trial(sp, A, b, *k, cur, delta, next, evals)) return OR_SEARCH_FAILED;
+    if (next->chi2 < cur->chi2) --*k;
+    while (cur->chi2 < next->chi2 && *k < 4 &&
+           !all_small(sp->P, sp->W, sp->H, delta, cur->p, sp->min_step)) {
+        ++*k;
+        if (damped_trial(sp, A, b, *k, cur, delta, next, evals)) return OR_SEARCH_FAILED;
+    }
+    if (isnan(next->chi2)) return OR_SEARCH_FAILED;
+    if (cur->chi2 < next->chi2)  /* R4: a step below minStep without decrease, or lambda 10^4 */
+        return all_small(sp->P, sp->W, sp->H, delta, cur->p, sp->min_step) ? OR_SEARCH_STALLED
+                                                                           : OR_SEARCH_FAILED;
+    return OR_SEARCH_DECREASED;
+}
+
+/* Stop tests after an accepted step from `from` (error chi_from) to an error chi_to, in the
+ * order of reading R10: maxError, minDelta (relative decrease), minStep (reading R6). */
+static int stop_test(const or_spot *sp, const or_point *from, double chi_to, const double *delta)
+{
+    if (chi_to < sp->max_error) return OR_MAX_ERROR;
+    if (from->chi2 * (1.0 - sp->min_delta) < chi_to) return OR_MIN_DELTA;
+    if (all_small(sp->P, sp->W, sp->H, delta, from->p, sp->min_step)) return OR_MIN_STEP;
+    return OR_CONTINUE;
+}
+
+/* One spot: the damped LM iteration of Sec. "Levenberg-Marquardt algorithm" with the stop
+ * criteria of the Fit2DGaussian listing. Every iteration evaluates the current point with
+ * its normal equations, runs the damping search and either moves to the trial point or
+ * stops. p0 is the caller's start point (4 values; the isotropic model uses p0[2] as sigma).
+ * Outputs p (4 values; isotropic writes sigma into both slots 2 and 3), alpha^, beta^,
+ * normalised chi^2, outcome, iterations and the number of evaluated points. trace
+ * (max_iter + 1 values, or NULL) receives the error at the start of every iteration followed
+ * by the final error; unused slots are NaN. */
 int or_fit_one(int model, int W, int H, const double *g, const double *p0, int max_iter,
                double max_error, double min_delta, double min_step, double *p_out,
                double *alpha_out, double *beta_out, double *chi2n_out, int *iters_out,
                int *evals_out, double *trace)
 {
-    const int P = or_nparams(model);
-    double p[4] = {p0[0], p0[1], p0[2], P == 4 ? p0[3] : p0[2]};
-    or_limit(model, W, H, p);
-    if (P == 3) p[3] = p[2];
+    const or_spot sp = {model, W, H, or_nparams(model), g, max_error, min_delta, min_step};
+    or_point cur = {{p0[0], p0[1], p0[2], sp.P == 4 ? p0[3] : p0[2]}, 0.0, 0.0, 0.0};
+    or_limit(model, W, H, cur.p);
+    if (sp.P == 3) cur.p[3] = cur.p[2];
     if (trace)
         for (int k = 0; k <= max_iter; ++k) trace[k] = NAN;
 
-    int k_lambda = -2; /* lambda = 10^k, initially 0.01 */
+    int k_lambda = -2; /* lambda = 10^k, 0.01 at the start of every fit (R11) */
     int it = 0, evals = 0, state = OR_MAX_ITER;
-    double A[4][4], b[4], best[4], delta[4], pt[4];
-
+    double A[4][4], b[4], delta[4];
     while (it < max_iter) {
         ++it;
-        double a, bb, chi;
         ++evals;
-        if (evaluate(model, W, H, g, p, &a, &bb, &chi, A, b)) chi = NAN;
-        if (trace) trace[it - 1] = chi;
-        if (isnan(chi)) { state = OR_NOT_CONVERGED; break; }
-        if (chi < max_error) { state = OR_MAX_ERROR; break; }
-        memcpy(best, p, sizeof best);
+        if (evaluate(model, W, H, g, cur.p, &cur.alpha, &cur.beta, &cur.chi2, A, b))
+            cur.chi2 = NAN;
+        if (trace) trace[it - 1] = cur.chi2;
+        if (isnan(cur.chi2)) { state = OR_NOT_CONVERGED; break; }
+        if (cur.chi2 < max_error) { state = OR_MAX_ERROR; break; }
 
-        double at, btt, Chi;
-        if (solve_damped(P, A, b, pow(10.0, k_lambda), delta)) { state = OR_NOT_CONVERGED; break; }
-        ++evals;
-        Chi = trial(model, W, H, g, best, delta, pt, &at, &btt);
-        if (chi > Chi) --k_lambda;
-        int failed_solve = 0;
-        while (!all_small(P, W, H, delta, best, min_step) && chi < Chi && k_lambda < 4) {
-            ++k_lambda;
-            if (solve_damped(P, A, b, pow(10.0, k_lambda), delta)) { failed_solve = 1; break; }
-            ++evals;
-            Chi = trial(model, W, H, g, best, delta, pt, &at, &btt);
-        }
-        if (failed_solve) { state = OR_NOT_CONVERGED; break; }
-        if (chi < Chi || isnan(Chi)) {
-            state = (all_small(P, W, H, delta, best, min_step) && !isnan(Chi)) ? OR_NO_DECREASE
-                                                                         : OR_NOT_CONVERGED;
-            break; /* p stays at best */
-        }
-        memcpy(p, pt, sizeof p);
-        if (Chi < max_error) { state = OR_MAX_ERROR; break; }
-        if (chi * (1.0 - min_delta) < Chi) { state = OR_MIN_DELTA; break; }
-        if (all_small(P, W, H, delta, best, min_step)) { state = OR_MIN_STEP; break; }
+        or_point next;
+        const int search = damping_search(&sp, A, b, &k_lambda, &cur, &next, delta, &evals);
+        if (search == OR_SEARCH_FAILED) { state = OR_NOT_CONVERGED; break; }
+        if (search == OR_SEARCH_STALLED) { state = OR_NO_DECREASE; break; }
+        const int stop = stop_test(&sp, &cur, next.chi2, delta);
+        cur = next; /* accepted: the search continues from the trial point */
+        if (stop != OR_CONTINUE) { state = stop; break; }
     }
 
     /* final error at the reported parameters (the listing's NormalizedChi) */
     double a, bb, chi;
-    if (evaluate(model, W, H, g, p, &a, &bb, &chi, NULL, NULL)) { a = bb = chi = NAN; }
+    if (evaluate(model, W, H, g, cur.p, &a, &bb, &chi, NULL, NULL)) { a = bb = chi = NAN; }
     if (trace) trace[it < max_iter ? it : max_iter] = chi;
-    for (int j = 0; j < 4; ++j) p_out[j] = p[j];
+    for (int j = 0; j < 4; ++j) p_out[j] = cur.p[j];
     *alpha_out = a;
     *beta_out = bb;
-    *chi2n_out = chi / (double)(W * H - P - 2);
+    *chi2n_out = chi / (double)(W * H - sp.P - 2);
     *iters_out = it;
     *evals_out = evals;
     return state;
@@ -414,9 +466,10 @@ void or_fit_spots(const void *images, int dtype, int64_t image_elems, const int6
         double p0[4] = {init[4 * s], init[4 * s + 1], init[4 * s + 2], init[4 * s + 3]};
         double *tr = trace ? trace + s * (int64_t)(max_iter + 1) : NULL;
         const int valid_model = (m == OR_MODEL_ISO || m == OR_MODEL_ELLIPTIC);
-        const int N = W * H;
-        if (!valid_model || W < 3 || H < 3 || W > OR_MAX_SIDE || H > OR_MAX_SIDE ||
-            N <= or_nparams(m) + 2 || off < 0 || off + N > image_elems) {
+        const int sides_ok = W >= 3 && H >= 3 && W <= OR_MAX_PIXELS / 3 && H <= OR_MAX_PIXELS / 3;
+        const int N = sides_ok ? W * H : 0;
+        if (!valid_model || !sides_ok || N > OR_MAX_PIXELS || N <= or_nparams(m) + 2 || off < 0 ||
+            off + N > image_elems) {
             for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p0[j];
             out_alpha[s] = out_beta[s] = out_chi2[s] = NAN;
             out_state[s] = OR_INVALID;

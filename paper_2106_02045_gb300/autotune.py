@@ -23,11 +23,15 @@ import torch
 
 from . import fitspots, synth
 
+# the classes with a choice: W, H <= 32 (class 16, a side above 32, has one configuration)
 NUM_CLASSES = 16
+ELONGATED_CLASS = 16
 
 
 def class_of(W: int, H: int) -> int:
     """Size class of a W x H spot."""
+    if W > 32 or H > 32:
+        return ELONGATED_CLASS
     return ((W + 7) // 8 - 1) * 4 + ((H + 7) // 8 - 1)
 
 
@@ -63,6 +67,9 @@ def _time_uniform(b: synth.SpotBatch, W: int, H: int, reps: int) -> float:
 def autotune(classes=None, n: int = 131072, reps: int = 3, dtype: int = fitspots.F32,
              device="cuda:0", cache: str | Path | None = None, seed: int = 20210610) -> dict:
     """Time every usable configuration of each class; keep and return the fastest.
+
+    The choice applies where a class runs in a launch of its own (fit_spots_uniform and
+    fit_spots_per_class); fit_spots runs every class in one launch of the generic kernel.
 
     Returns {class: {"config": c, "ms": t, "tried": {config: ms}}} and, with ``cache``,
     merges the choice into that JSON file under the device's name and the pixel type.
@@ -116,8 +123,8 @@ def load(cache: str | Path, dtype: int = fitspots.F32, device="cuda:0") -> dict:
 
 
 def defaults() -> None:
-    """Restore the width-bound default configuration of every class."""
-    for cls in range(NUM_CLASSES):
+    """Restore the built-in configuration of every class."""
+    for cls in range(fitspots.num_classes()):
         fitspots.set_config(cls, default_config(cls))
 
 

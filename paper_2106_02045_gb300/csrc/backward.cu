@@ -723,7 +723,7 @@ extern "C" int fit_spots_backward(const void *images, int dtype, int64_t image_e
                                   const float *grad_params, const float *grad_alpha,
                                   const float *grad_beta, const float *grad_chi2,
                                   float *grad_images, void *stream) {
-  if (n < 0 || n > INT32_MAX || image_elems < 0) return FS_ERR_SIZE;
+  if (n < 0 || n > FS_MAX_SPOTS || image_elems < 0) return FS_ERR_SIZE;
   if (dtype != FS_U16 && dtype != FS_F32) return FS_ERR_DTYPE;
   if (n == 0) return FS_OK;
   if (!images || !offsets || !roi_dims || !model || !params || !alpha || !beta || !state ||

@@ -46,6 +46,8 @@ def library() -> ctypes.CDLL:
         lib.fit_spots.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
                                   vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fit_spots.restype = i
+        lib.fit_spots_per_class.argtypes = lib.fit_spots.argtypes
+        lib.fit_spots_per_class.restype = i
         lib.fit_spots_uniform.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
                                           vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fit_spots_uniform.restype = i
@@ -59,6 +61,11 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_uniform_host.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
                                                vp, vp, vp, vp, vp, vp, vp, i64, vp, sz, vp]
         lib.fit_spots_uniform_host.restype = i
+        lib.fit_spots_noalloc.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
+                                          vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.fit_spots_noalloc.restype = i
+        lib.fit_spots_noalloc_max_spots.argtypes = []
+        lib.fit_spots_noalloc_max_spots.restype = i64
         lib.fit_spots_uniform_host_workspace.argtypes = [i64, i, i, i]
         lib.fit_spots_uniform_host_workspace.restype = sz
         lib.fit_spots_uniform_workspace.argtypes = []
@@ -67,6 +74,13 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_default_config.restype = i
         lib.fit_spots_config_batched.argtypes = [i]
         lib.fit_spots_config_batched.restype = i
+        lib.fit_spots_probe_scratch_bytes.argtypes = [i]
+        lib.fit_spots_probe_scratch_bytes.restype = sz
+        lib.fit_spots_probe_rates.argtypes = [i, vp, sz, ctypes.POINTER(d), ctypes.POINTER(d),
+                                              ctypes.POINTER(d), vp]
+        lib.fit_spots_probe_rates.restype = i
+        lib.fit_spots_config_generic.argtypes = [i]
+        lib.fit_spots_config_generic.restype = i
         lib.fit_spots_config_fits.argtypes = [i, i]
         lib.fit_spots_config_fits.restype = i
         lib.fit_spots_backward.argtypes = [vp, i, i64, vp, vp, vp, i64, vp, vp, vp, vp,
@@ -136,9 +150,12 @@ def alloc_outputs(n: int, device) -> dict:
 def fit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor, init: torch.Tensor,
         model: torch.Tensor, *, max_iter: int = 20, max_error: float = 0.0,
         min_delta: float = 1e-6, min_step: float = 1e-4, out: dict | None = None,
-        workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None) -> dict:
+        workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None,
+        per_class: bool = False) -> dict:
     """Fit all spots; returns (or fills ``out``) params [n,4], alpha, beta, chi2 (normalised),
-    state, iters, evals. Asynchronous on ``stream`` (default: the current stream)."""
+    state, iters, evals. Asynchronous on ``stream`` (default: the current stream).
+    ``per_class`` runs fit_spots_per_class (one persistent launch per size class, each with
+    its configured kernel) instead of the single generic launch of fit_spots."""
     dev = images.device
     if dev.type != "cuda":
         raise FitSpotsError("images must be a CUDA tensor")
@@ -164,7 +181,8 @@ def fit(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor, init: t
         o = out if out is not None else alloc_outputs(n, dev)
         if workspace is None:
             workspace = torch.empty(max(workspace_bytes(n), 16), dtype=torch.uint8, device=dev)
-        rc = library().fit_spots(
+        fn = library().fit_spots_per_class if per_class else library().fit_spots
+        rc = fn(
             _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), _ptr(init), _ptr(model),
             n, int(max_iter), float(max_error), float(min_delta), float(min_step),
             _ptr(o["params"]), _ptr(o["alpha"]), _ptr(o["beta"]), _ptr(o["chi2"]), _ptr(o["state"]),
@@ -362,6 +380,32 @@ def default_config(size_class: int) -> int:
     c = int(library().fit_spots_default_config(int(size_class)))
     check(min(c, 0), "fit_spots_default_config")
     return c
+
+
+def config_generic(config: int) -> bool:
+    """Whether ``config`` is the generic configuration (fit_spots' single launch)."""
+    c = int(library().fit_spots_config_generic(int(config)))
+    check(min(c, 0), "fit_spots_config_generic")
+    return bool(c)
+
+
+def probe_rates(device="cuda:0") -> dict:
+    """Measured lane-operations per second of FP32 FMA, MUFU exp2 and FP64 FMA on ``device``
+    (the roofline denominators of the fit kernels); see fit_spots_probe_rates."""
+    dev = torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    lib = library()
+    scratch = torch.empty(int(lib.fit_spots_probe_scratch_bytes(sms)), dtype=torch.uint8, device=dev)
+    f, e, dd = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    s = torch.cuda.current_stream(dev)
+    check(lib.fit_spots_probe_rates(sms, _ptr(scratch), scratch.numel(), ctypes.byref(f),
+                                    ctypes.byref(e), ctypes.byref(dd), ctypes.c_void_p(s.cuda_stream)),
+          "fit_spots_probe_rates")
+    return {"ffma": f.value, "ex2": e.value, "dfma": dd.value, "sms": sms}
+
+
+def num_classes() -> int:
+    return int(library().fit_spots_num_classes())
 
 
 def config_fits(size_class: int, config: int) -> bool:

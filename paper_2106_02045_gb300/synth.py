@@ -19,6 +19,9 @@ pixel centre):
   capped at min(W, H)/4; centre (W-1)/2, (H-1)/2 +- U(1); spot offsets are padded to
   4-element (16-byte) boundaries.
 * ``iso16``   262,144 spots, 16x16 float32, isotropic like ``iso15``, centre 7.5 +- U(1).
+* ``elongated`` 200,000 spots with a side above 32 and at most 1024 pixels (64x16, 128x8,
+  40x25, 100x10, 256x4, 341x3, 33x31 and their transposes, uniformly), both models, drawn
+  like ``mixed``.
 * ``paper``   the accuracy protocol of the paper's Results section: S x S, centre
   N(0, S/20) around the ROI centre, sigma ~ U(1, 2), integrated signal and total
   background given in counts, Gaussian noise of variance equal to the pixel value,
@@ -39,8 +42,9 @@ import torch
 
 MODEL_ISO, MODEL_ELLIPTIC = 0, 1
 SEED_BASE = 20210603
-WORKLOADS = ("iso15", "ell32", "mixed", "iso16")
-FULL_SIZES = {"iso15": 10_000, "ell32": 1_000_000, "mixed": 2_000_000, "iso16": 262_144}
+WORKLOADS = ("iso15", "ell32", "mixed", "iso16", "elongated")
+FULL_SIZES = {"iso15": 10_000, "ell32": 1_000_000, "mixed": 2_000_000, "iso16": 262_144,
+              "elongated": 200_000}
 
 
 @dataclass
@@ -209,6 +213,31 @@ def make_mixed(n: int, seed: int = SEED_BASE + 3, device="cpu", name="mixed") ->
     Ws = torch.randint(5, 33, (n,), generator=gen, device=device)
     Hs = torch.randint(5, 33, (n,), generator=gen, device=device)
     models = (torch.rand(n, generator=gen, device=device) < 0.5).to(torch.uint8)
+    return _pack_sized(Ws, Hs, models, gen, device, name)
+
+
+# elongated shapes: a side above 32 and at most 1024 pixels, both orientations
+ELONGATED_SHAPES = ((64, 16), (16, 64), (128, 8), (8, 128), (40, 25), (25, 40), (100, 10),
+                    (10, 100), (256, 4), (4, 256), (341, 3), (3, 341), (33, 31), (31, 33))
+
+
+def make_elongated(n: int, seed: int = SEED_BASE + 5, device="cpu",
+                   shapes=ELONGATED_SHAPES, name="elongated") -> SpotBatch:
+    """ROIs with a side above 32 (the paper's bound is 1024 pixels per fit, not a side):
+    shapes drawn uniformly from ``shapes``, both models, drawn like ``mixed`` (float32)."""
+    gen = _gen(seed, device)
+    pick = torch.randint(0, len(shapes), (n,), generator=gen, device=device)
+    table = torch.tensor(shapes, dtype=torch.int64, device=device)
+    Ws, Hs = table[pick, 0], table[pick, 1]
+    models = (torch.rand(n, generator=gen, device=device) < 0.5).to(torch.uint8)
+    return _pack_sized(Ws, Hs, models, gen, device, name)
+
+
+def _pack_sized(Ws, Hs, models, gen, device, name) -> SpotBatch:
+    """Spots of the given sizes and models: isotropic ones drawn like ``iso15``, elliptic
+    ones like ``ell32`` (as float32), every sigma capped at min(W, H) / 4, the centre within
+    1 px of the ROI centre; offsets padded to 4-element (16-byte) boundaries."""
+    n = Ws.numel()
     n_el = (Ws * Hs).to(torch.int64)
     span = (n_el + 3) // 4 * 4
     offsets = torch.cumsum(span, 0) - span
@@ -217,11 +246,11 @@ def make_mixed(n: int, seed: int = SEED_BASE + 3, device="cpu", name="mixed") ->
     tp = torch.empty((n, 4), dtype=torch.float64, device=device)
     ta = torch.empty(n, dtype=torch.float64, device=device)
     tb = torch.empty(n, dtype=torch.float64, device=device)
-    key = (Ws * 64 + Hs) * 2 + models.to(torch.int64)
+    key = (Ws * 1024 + Hs) * 2 + models.to(torch.int64)
     for k in torch.unique(key).tolist():
         idx = torch.nonzero(key == k).flatten()
         m = int(k % 2)
-        W, H = int(k // 2 // 64), int(k // 2 % 64)
+        W, H = int(k // 2 // 1024), int(k // 2 % 1024)
         cnt = idx.numel()
         cap = min(W, H) / 4.0
         x = (W - 1) / 2 + _uniform(cnt, -1.0, 1.0, gen, device)
@@ -334,6 +363,8 @@ def make_workload(name: str, n: int | None = None, device="cpu") -> SpotBatch:
         return make_mixed(n, SEED_BASE + 3, device, name)
     if name == "iso16":
         return make_iso(n, 16, 7.5, SEED_BASE + 4, device, name)
+    if name == "elongated":
+        return make_elongated(n, SEED_BASE + 5, device, name=name)
     raise KeyError(name)
 
 

@@ -36,8 +36,9 @@ def test_every_declared_function_is_exported(lib):
 def test_workspace_sizes(lib):
     assert lib.fit_spots_workspace(0) == 0
     assert lib.fit_spots_workspace(-5) == 0
-    assert lib.fit_spots_workspace(1000) == 256 + 4 * 1000
-    assert lib.fit_spots_uniform_workspace() == 256
+    # the schedule header: counts, starts, cursors and fill cursors of the 17 size classes
+    assert lib.fit_spots_workspace(1000) == 272 + 4 * 1000
+    assert lib.fit_spots_uniform_workspace() == 272
 
 
 def _call(lib, **over):
@@ -79,10 +80,12 @@ def test_argument_checks(lib):
 def test_uniform_argument_checks(lib):
     fake = ctypes.c_void_p(0x1000)
 
-    def call(W=32, H=32, model=1, n=10, ws=fake, ws_bytes=256, max_iter=20):
+    def call(W=32, H=32, model=1, n=10, ws=fake, ws_bytes=272, max_iter=20):
         return lib.fit_spots_uniform(fake, 0, W, H, model, fake, n, max_iter, 0.0, 1e-6, 1e-4,
                                      fake, fake, fake, fake, fake, fake, None, ws, ws_bytes, None)
-    assert call(W=2) == -8 and call(H=33) == -8 and call(model=3) == -8
+    assert call(W=2) == -8 and call(H=3, W=342) == -8 and call(model=3) == -8
+    assert call(W=33, H=32) == -8                       # 1056 pixels: above the 1024 bound
+    assert call(W=64, H=16, n=0) == 0 and call(W=3, H=341, n=0) == 0   # elongated ROIs
     assert call(n=0) == 0
     assert call(ws_bytes=16) == -6
     assert call(ws=None) == -1
@@ -95,10 +98,11 @@ def test_host_call_argument_checks(lib):
     one = lib.fit_spots_uniform_host_workspace(1000, 32, 32, 0)
     # per chunk buffer: images, start values, 7 outputs, schedule header; 256-byte aligned
     up = lambda v: (v + 255) // 256 * 256
-    assert one == 2 * (up(1000 * 32 * 32 * 2) + 2 * up(16000) + 5 * up(4000) + up(4000) + 256)
+    assert one == 2 * (up(1000 * 32 * 32 * 2) + 2 * up(16000) + 5 * up(4000) + up(4000) + up(272))
     assert lib.fit_spots_uniform_host_workspace(1000, 32, 32, 1) > one
     assert lib.fit_spots_uniform_host_workspace(0, 32, 32, 0) == 0
-    assert lib.fit_spots_uniform_host_workspace(10, 33, 32, 0) == 0
+    assert lib.fit_spots_uniform_host_workspace(10, 33, 32, 0) == 0      # 1056 pixels
+    assert lib.fit_spots_uniform_host_workspace(10, 64, 16, 0) > 0       # elongated
     assert lib.fit_spots_uniform_host_workspace(10, 32, 32, 5) == 0
     fake = ctypes.c_void_p(0x1000)
 
@@ -172,18 +176,33 @@ def test_serving_argument_checks(lib):
 
 def test_spot_count_limit(lib):
     """FS_MAX_SPOTS (2^31 - 2^24) leaves the kernels' 32-bit work counters headroom: the
-    header's value is the binding's, and the calls that check it reject one spot more
-    before any CUDA work."""
+    header's value is the binding's, and every C entry point that takes a spot count
+    rejects one spot more before any CUDA work (checked in C, no Python guard on the way)."""
     from paper_2106_02045_gb300 import fitspots
     text = (ROOT / "include" / "fitspots.h").read_text()
     m = re.search(r"#define FS_MAX_SPOTS (\d+)LL", text)
     assert m and int(m.group(1)) == fitspots.MAX_SPOTS == 2**31 - 2**24
-    over = fitspots.MAX_SPOTS + 1
+    top = fitspots.MAX_SPOTS
+    over = top + 1
     fake = ctypes.c_void_p(0x1000)
     assert lib.fit_spots_start(fake, 0, 100, fake, fake, over, 0, fake, None) == -2
-    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted):
+    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted, lib.fit_spots_noalloc):
         assert fn(fake, 0, 100, fake, fake, fake, fake, over, 20, 0.0, 1e-6, 1e-4,
                   fake, fake, fake, fake, fake, fake, None, None) == -2
+    # the workspace calls: one spot more is a size error, the limit itself gets as far as
+    # the workspace check (dummy pointers, so nothing is ever enqueued)
+    assert _call(lib, n=over) == -2
+    assert _call(lib, n=top, ws_bytes=272) == -6
+    uni = lambda n: lib.fit_spots_uniform(fake, 0, 32, 32, 1, fake, n, 20, 0.0, 1e-6, 1e-4,
+                                         fake, fake, fake, fake, fake, fake, None, fake, 16, None)
+    assert uni(over) == -2 and uni(top) == -6
+    host = lambda n: lib.fit_spots_uniform_host(fake, 0, 32, 32, 1, fake, n, 20, 0.0, 1e-6,
+                                                1e-4, fake, fake, fake, fake, fake, fake, None,
+                                                1000, fake, 16, None)
+    assert host(over) == -2 and host(top) == -6
+    bwd = lambda n: lib.fit_spots_backward(fake, 1, 100, fake, fake, fake, n, fake, fake, fake,
+                                           fake, None, None, None, None, fake, None)
+    assert bwd(over) == -2
     with pytest.raises(fitspots.FitSpotsError, match="at most"):
         fitspots._check_count(over)
     fitspots._check_count(fitspots.MAX_SPOTS)
@@ -191,25 +210,34 @@ def test_spot_count_limit(lib):
 
 def test_size_classes_and_configs(lib):
     from paper_2106_02045_gb300 import fitspots
-    assert lib.fit_spots_num_classes() == 16
+    assert lib.fit_spots_num_classes() == 17
     cfgs = fitspots.configs()
-    assert len(cfgs) == lib.fit_spots_num_configs() == 56
-    assert sum(c[3] for c in cfgs) == 20 and lib.fit_spots_config_batched(99) == -8
+    assert len(cfgs) == lib.fit_spots_num_configs() == 58
+    assert sum(c[3] for c in cfgs) == 22 and lib.fit_spots_config_batched(99) == -8
+    generic, elong = 56, 57   # one column per lane, each ROI oriented; row blocks for class 16
+    assert cfgs[generic] == (32, 1, 32, 1) and cfgs[elong] == (32, 1, 32, 1)
+    assert fitspots.config_generic(generic) and fitspots.config_generic(elong)
+    assert not fitspots.config_generic(55)
     for cls in range(16):
         wmax, hmax = (cls // 4 + 1) * 8, (cls % 4 + 1) * 8
         usable = [c for c in range(len(cfgs)) if fitspots.config_fits(cls, c)]
         assert usable, cls
         for c in usable:
             L, C, R, batched = cfgs[c]
-            assert L * C >= wmax and L * C < wmax + 8 and R == hmax and 32 % L == 0
-        assert fitspots.get_config(cls) in usable
+            if c == generic:   # takes any ROI up to 32 x 32, oriented
+                continue
+            assert L * C >= wmax and L * C <= 32 and R == hmax and 32 % L == 0
+        assert fitspots.get_config(cls) in usable and generic in usable and elong not in usable
+    # the elongated class (a side above 32) runs the row-block configuration and nothing else
+    assert [c for c in range(len(cfgs)) if fitspots.config_fits(16, c)] == [elong]
+    assert fitspots.default_config(16) == elong
     assert lib.fit_spots_set_config(15, 0) == -8          # (4,2,8) cannot hold 32x32
     keep = fitspots.get_config(15)
     other = [c for c in range(len(cfgs)) if fitspots.config_fits(15, c) and c != keep][0]
     fitspots.set_config(15, other)
     assert fitspots.get_config(15) == other
     fitspots.set_config(15, keep)
-    assert lib.fit_spots_get_config(16) == -8 and lib.fit_spots_config_info(99, None, None, None) == -8
+    assert lib.fit_spots_get_config(17) == -8 and lib.fit_spots_config_info(99, None, None, None) == -8
 
 
 def test_binding_refuses_cpu_tensors():

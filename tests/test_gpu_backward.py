@@ -158,12 +158,25 @@ def test_backward_matches_oracle_uint16_ell32():
 
 
 def test_backward_identities_both_models():
-    """Shift and scale invariance of the fit fix sum_i dq/dg_i and sum_i g_i dq/dg_i."""
+    """Shift and scale invariance of the fit fix sum_i dq/dg_i and sum_i g_i dq/dg_i. They hold
+    at the exact minimum, so the backward kernel is evaluated at the oracle's polished FP64
+    fit of each spot (the forward kernel's FP32 stop can lie off the minimum by more than the
+    identities' tolerance); this checks the backward alone."""
+    import oracle
     for name in ("iso16", "ell32"):
-        b = synth.make_workload(name, 256, device=DEV)   # ell32 stays uint16
-        out = fitspots.fit_batch(b, **TIGHT)
+        b = synth.make_workload(name, 256)   # ell32 stays uint16
+        d = b.numpy()
+        ref = oracle.fit_spots(synth.as_numpy_images(b), d["offsets"], d["dims"], d["init"],
+                               d["model"], max_iter=300, min_delta=0.0, min_step=1e-13)
+        b = b.to(DEV)
+        out = {k: torch.as_tensor(ref[k], device=DEV).to(torch.float32)
+               for k in ("params", "alpha", "beta", "chi2")}
+        out["state"] = torch.as_tensor(ref["state"], device=DEV)
         conv = torch.isin(out["state"], torch.tensor(fitspots.CONVERGED_STATES, device=DEV,
                                                      dtype=torch.int32))
+        # spots whose amplitude stands above the residual noise: a well-defined minimum
+        conv &= out["alpha"] > 3.0 * torch.sqrt(out["chi2"].clamp_min(0.0))
+        assert conv.sum() >= 100
         N = int(b.dims[0, 0] * b.dims[0, 1])
         gimg = b.images.to(torch.float32).view(b.n, N).double()
         for k, name_k in enumerate(("x0", "y0", "sx", "sy", "alpha", "beta", "chi2")):

@@ -1,5 +1,6 @@
 """The batched kernel (one lane per spot for the LM step, the warp for the pixel passes; the
-default for ROIs 25..32 wide) against the per-spot kernel with one column per thread. They
+default for ROIs 25..32 wide when a class runs alone) against the per-spot kernel with one
+column per thread. They
 share the evaluation and the LM step but not the FP32 contraction of every expression, so
 results agree to rounding, and a few spots whose fit ends within rounding of a stop
 threshold take a different stop; the oracle parity tests cover the batched kernel's
@@ -67,7 +68,7 @@ def _agree(a, c, sel):
                                 dict(max_iter=1), dict(max_iter=3, max_error=5e3)])
 def test_batched_agrees_with_per_spot_kernel_on_mixed_sizes(kw):
     b = synth.make_workload("mixed", 20000, device=DEV)
-    a, c = _both(lambda: fitspots.fit_batch(b, **kw))
+    a, c = _both(lambda: fitspots.fit_batch(b, per_class=True, **kw))
     wide = ((b.dims[:, 0] + 7) // 8 == 4).cpu().numpy()
     assert wide.sum() > 2000
     for k in a:   # the narrower classes run the same kernel either way

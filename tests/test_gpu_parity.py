@@ -100,10 +100,75 @@ def test_full_size_mixed_sampled():
     assert np.isin(st, (1, 2, 3, 4)).mean() > 0.9 and not np.isin(st, (-2,)).any()
 
 
+def test_elongated_rois_against_oracle():
+    """ROIs with a side above 32 (at most 1024 pixels, the paper's bound on one fit): 64x16,
+    128x8, 341x3, 33x31 and their transposes, both models, through the single launch of
+    fit_spots (the elongated class: short side along the lanes, long side in row blocks)."""
+    b = synth.make_workload("elongated", 6000)
+    out = _fit(b)
+    ref = run_oracle(b)
+    m = compare(out, ref, b.dims.numpy(), determined(b, ref))
+    _report("elongated", m)
+    assert not np.isin(out["state"], (-2,)).any()
+    assert m["n_well_posed"] >= 0.25 * b.n
+    assert m["class_agree_wp"] >= 0.999 and m["bar_wp"] >= 0.999
+    assert m["class_agree"] >= 0.99
+    # every shape and orientation took part
+    shapes = {tuple(d) for d in b.dims.numpy()[np.isin(out["state"], (1, 2, 3, 4))].tolist()}
+    assert shapes == set(synth.ELONGATED_SHAPES)
+
+
+def test_single_launch_and_per_class_launches():
+    """fit_spots runs every size class in one persistent launch of the generic configuration;
+    fit_spots_per_class gives each class a launch of its own with its configured kernel. With
+    every class configured to the generic kernel the two are the same arithmetic (identical
+    bits); with the built-in per-class kernels they agree like two kernels of different
+    geometry (FP32 sums in another order)."""
+    from tests.test_gpu_batched import _agree
+    mixed = synth.make_workload("mixed", 6000, device=DEV)
+    elong = synth.make_workload("elongated", 1500, device=DEV)
+    keep = [fitspots.get_config(c) for c in range(16)]
+    generic = [c for c in range(len(fitspots.configs()))
+               if fitspots.config_generic(c) and fitspots.config_fits(0, c)][0]
+    try:
+        for c in range(16):   # the classes of W, H <= 32 (the elongated class has its own)
+            fitspots.set_config(c, generic)
+        for b in (mixed, elong):
+            o1 = fitspots.fit_batch(b)
+            o2 = fitspots.fit_batch(b, per_class=True)
+            torch.cuda.synchronize()
+            for k in o1:
+                assert torch.equal(o1[k].view(torch.int32), o2[k].view(torch.int32)), (b.name, k)
+    finally:
+        for c, k in enumerate(keep):
+            fitspots.set_config(c, k)
+    o1 = to_numpy(fitspots.fit_batch(mixed))
+    o2 = to_numpy(fitspots.fit_batch(mixed, per_class=True))
+    same_class, ok, nboth = _agree(o1, o2, np.ones(mixed.n, bool))
+    print(f"single vs per-class launches: same class {same_class:.4f}, within the bar {ok:.4f}")
+    assert same_class >= 0.995 and ok >= 0.98
+
+
+def test_uniform_elongated_calls_agree_with_general_bitwise():
+    """fit_spots_uniform takes elongated sizes too (wide ones fitted transposed)."""
+    # pixel counts divisible by 4, so that the packed batch is also the back-to-back layout
+    for W, H, m in ((64, 16, 1), (16, 64, 0), (40, 25, 1), (8, 128, 1), (256, 4, 0)):
+        b = synth.make_elongated(700, seed=77 + W, device=DEV, shapes=((W, H),))
+        keep = b.model.clone().fill_(m)
+        b.model.copy_(keep)
+        o1 = fitspots.fit_batch(b)
+        o2 = fitspots.fit_uniform(b.images, W, H, m, b.init)
+        torch.cuda.synchronize()
+        assert (o1["state"] != -2).all()
+        for k in o1:
+            assert torch.equal(o1[k].view(torch.int32), o2[k].view(torch.int32)), (W, H, k)
+
+
 def test_uniform_and_general_entry_points_agree_bitwise():
+    """A class that runs alone uses its configured kernel through either entry point."""
     for name in ("iso15", "ell32"):
         b = synth.make_workload(name, 3000, device=DEV)
-        o1 = fitspots.fit_batch(b)
+        o1 = fitspots.fit_batch(b, per_class=True)
         W, H = int(b.dims[0, 0]), int(b.dims[0, 1])
         o2 = fitspots.fit_uniform(b.images, W, H, int(b.model[0]), b.init)
         torch.cuda.synchronize()
@@ -166,12 +231,12 @@ def test_edge_cases():
     b = synth.make_workload("iso15", 64, device=DEV)
     empty = fitspots.fit(b.images, b.offsets[:0], b.dims[:0], b.init[:0], b.model[:0])
     assert empty["state"].numel() == 0
-    # invalid spots: too small, too large, bad model, offset past the end
+    # invalid spots: too small, too large (1056 pixels), bad model, offset past the end
     dims = b.dims.clone()
     model = b.model.clone()
     offs = b.offsets.clone()
     dims[0] = torch.tensor([2, 15])
-    dims[1] = torch.tensor([33, 15])
+    dims[1] = torch.tensor([33, 32])
     model[2] = 9
     offs[3] = b.images.numel() - 10
     imgs = b.images.clone()

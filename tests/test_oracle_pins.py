@@ -217,6 +217,56 @@ def test_exact_recovery_of_noise_free_spots(oracle_mod, model):
         assert abs(o["beta"][s] - bg) < 1e-9 * max(amp, 1.0)
 
 
+@pytest.mark.parametrize("model", [ISO, ELL])
+def test_exact_recovery_of_elongated_spots(oracle_mod, model):
+    """ROIs with a side above 32 (up to 1024 pixels, the paper's bound on one fit): noise-free
+    spots are recovered to better than 1e-9, in both orientations."""
+    rng = np.random.default_rng(17 + model)
+    shapes = [(64, 16), (16, 64), (128, 8), (8, 128), (341, 3), (3, 341), (40, 25), (100, 10)]
+    spots, dims, init, truth = [], [], [], []
+    for W, H in shapes * 2:
+        cap = min(W, H) / 4
+        p = np.array([(W - 1) / 2 + rng.uniform(-1, 1), (H - 1) / 2 + rng.uniform(-1, 1),
+                      rng.uniform(0.6, max(0.7, min(2.5, cap))),
+                      rng.uniform(0.6, max(0.7, min(2.5, cap)))])
+        if model == ISO:
+            p[3] = p[2]
+        amp, bg = rng.uniform(500, 5000), rng.uniform(0, 500)
+        spots.append(_spot(model, W, H, p, amp, bg, noise=False))
+        dims.append((W, H))
+        q = p + np.array([rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), 0, 0])
+        q[2] *= rng.uniform(0.85, 1.15)
+        q[3] = q[2] if model == ISO else q[3] * rng.uniform(0.85, 1.15)
+        init.append(q)
+        truth.append((p, amp, bg))
+    img, offs, dims = _pack(spots, dims)
+    o = oracle_mod.fit_spots(img, offs, dims, np.array(init, np.float32),
+                             np.full(len(spots), model, np.uint8), max_iter=100,
+                             min_delta=0.0, min_step=1e-12)
+    for s, (p, amp, bg) in enumerate(truth):
+        assert np.max(np.abs(o["params"][s] - p)) < 1e-9, (s, o["state"][s], o["params"][s], p)
+        assert abs(o["alpha"][s] - amp) < 1e-9 * amp
+        assert abs(o["beta"][s] - bg) < 1e-9 * max(amp, 1.0)
+
+
+def test_transpose_symmetry_on_elongated_spots(oracle_mod):
+    """A wide ROI and its transpose (64x16 / 16x64, 128x8 / 8x128) give the same fit with x and
+    y swapped: the elongated ROIs keep the exact symmetry of the method."""
+    rng = np.random.default_rng(23)
+    for W, H in ((64, 16), (128, 8), (200, 5)):
+        p = np.array([(W - 1) / 2 + 0.7, (H - 1) / 2 - 0.4, 1.8, 1.3])
+        g = _spot(ELL, W, H, p, 900, 80, rng).reshape(H, W)
+        s0 = np.array([p[0] + 0.3, p[1] - 0.2, 1.5, 1.5], np.float32)
+        img, offs, dd = _pack([g.ravel(), g.T.copy().ravel()], [(W, H), (H, W)])
+        init = np.array([s0, s0[[1, 0, 3, 2]]], np.float32)
+        o = oracle_mod.fit_spots(img, offs, dd, init, np.full(2, ELL, np.uint8), max_iter=300,
+                                 min_delta=0.0, min_step=1e-10)
+        q = o["params"]
+        assert np.isin(o["state"], (1, 2, 3, 4)).all()
+        assert np.allclose(q[1], q[0][[1, 0, 3, 2]], atol=1e-7)
+        assert abs(o["alpha"][1] - o["alpha"][0]) < 1e-7 * o["alpha"][0]
+
+
 def test_accepted_steps_never_increase_chi2(oracle_mod):
     b = synth.make_workload("ell32", 400)
     d = b.numpy()
@@ -395,6 +445,7 @@ def test_symmetries_on_random_spots(oracle_mod, model):
 def test_invalid_spots_are_flagged(oracle_mod):
     img = np.ones(4096, np.float32)
     offs = np.array([0, 100, 200, 300, 4000], np.int64)
+    # too narrow, 1089 pixels (above 1024), too flat, unknown model, past the end
     dims = np.array([[2, 10], [33, 33], [3, 2], [5, 5], [10, 10]], np.int32)
     model = np.array([0, 0, 1, 7, 0], np.uint8)
     o = oracle_mod.fit_spots(img, offs, dims, np.ones((5, 4), np.float32), model)

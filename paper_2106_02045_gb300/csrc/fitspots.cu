@@ -1071,13 +1071,12 @@ extern __shared__ float4 g_smem4[];
 
 // The LM step of slot j (Eq. 6 in FP64, accept / reject and the damping schedule, the stop
 // tests, the normal equations of Eq. 12-13 and the damped solve of Eq. 14 in FP64) on the
-// slot's own lane, from the evaluation results the warp left in shared memory. Not inlined:
-// its double-precision working set then never competes with the pixel passes for registers.
+// slot's own lane, from the evaluation results the warp left in shared memory.
 // wf is the warp's stride in the block's shared memory, yc0 the row-weight origin of the
 // geometry; origin selects the row-weight origin of the slot's evaluation (0: yc0, 1: half
 // its rows rounded up to 8, 2: half its rows).
 // Returns whether the slot is still active.
-__device__ __noinline__ bool lm_step(const FitArgs &a, const int wf, const int j, const float yc0,
+__device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const int j, const float yc0,
                                      const int origin) {
   float *const st = reinterpret_cast<float *>(g_smem4) + (threadIdx.x >> 5) * wf;
   const float *const res = st + kSlotFields * kSlots;
@@ -1381,9 +1380,22 @@ __device__ __forceinline__ void eval_one_column(const FitArgs &a, float *const s
       float s0 = 0.f;
       for (int b = nb - 1; b >= 0; --b) {
         if (b != nb - 1) load_rows<32, 1, R>(a, off, cs, rs, W, H, x, b * R, false, shift, g2);
+        if constexpr (kElong) {
 #pragma unroll
-        for (int y = 0; y < R; ++y)
-          if (!kElong || b * R + y < H) s0 = fmaf(tab[b * R + y], g[y], s0);  // rows of the spot
+          for (int y = 0; y < R; ++y)
+            if (b * R + y < H) s0 = fmaf(tab[b * R + y], g[y], s0);  // rows of the spot
+        } else {
+          // four rows of the table per 16-byte broadcast read
+          const float4 *const t4 = reinterpret_cast<const float4 *>(tab);
+#pragma unroll
+          for (int q = 0; q < R / 4; ++q) {
+            const float4 e = t4[q];
+            s0 = fmaf(e.x, g[4 * q], s0);
+            s0 = fmaf(e.y, g[4 * q + 1], s0);
+            s0 = fmaf(e.z, g[4 * q + 2], s0);
+            s0 = fmaf(e.w, g[4 * q + 3], s0);
+          }
+        }
       }
       red[lg] = ex * s0;
     }
@@ -1414,17 +1426,24 @@ __device__ __forceinline__ void eval_one_column(const FitArgs &a, float *const s
       for (int b = 0; b < nb; ++b) {
         if (b != 0) load_rows<32, 1, R>(a, off, cs, rs, W, H, x, b * R, false, shift, g2);
 #pragma unroll
-        for (int y = 0; y < R; ++y) {
-          if (!kElong || b * R + y < H) {  // padding rows hold zeros
-            const float e = tab[b * R + y];
-            const float yy = (float)(b * R + y) - yc;
-            const float u = fmaf(ca, e, g[y]);
-            if (y & 1) ch1 = fmaf(u, u, ch1);
-            else ch0 = fmaf(u, u, ch0);
-            const float w = e * u;
-            t0 += w;
-            t1 = fmaf(yy, w, t1);
-            t2 = fmaf(yy * yy, w, t2);
+        for (int q = 0; q < R / 4; ++q) {
+          // four rows of the table per 16-byte broadcast read (one row at a time in row blocks)
+          const float4 e4 = kElong ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : reinterpret_cast<const float4 *>(tab)[q];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int y = 4 * q + r;
+            if (!kElong || b * R + y < H) {  // padding rows hold zeros
+              const float e = kElong ? tab[b * R + y] : r == 0 ? e4.x : r == 1 ? e4.y : r == 2 ? e4.z : e4.w;
+              const float yy = (float)(b * R + y) - yc;
+              const float u = fmaf(ca, e, g[y]);
+              if (y & 1) ch1 = fmaf(u, u, ch1);
+              else ch0 = fmaf(u, u, ch0);
+              const float w = e * u;
+              t0 += w;
+              t1 = fmaf(yy, w, t1);
+              t2 = fmaf(yy * yy, w, t2);
+            }
           }
         }
       }

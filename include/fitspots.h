@@ -65,6 +65,7 @@ extern "C" {
 #define FS_ERR_WORKSPACE (-6)  /* workspace smaller than fit_spots_workspace(n)     */
 #define FS_ERR_CUDA (-7)       /* a CUDA call failed; see fit_spots_last_cuda_error  */
 #define FS_ERR_ARG (-8)        /* another argument is out of range                   */
+#define FS_ERR_FULL (-9)       /* serving: the frame queue is full, frame rejected   */
 
 /*
  * Largest spot count per call. The kernels hand out spots through 32-bit counters that
@@ -250,18 +251,87 @@ int fit_spots_backward(const void *images, int dtype, int64_t image_elems,
  * fs_serve_update: after fit_spots_uniform on the count*markers ROIs, move every marker
  * whose fit converged (state MIN_DELTA, MIN_STEP, MAX_ERROR or NO_DECREASE, finite
  * parameters) to origin + fitted centre (a lost marker keeps its last state), and write
- * results[b*markers + m][8] = (x, y, sigma_x, sigma_y in frame coordinates, alpha, beta,
- * normalised chi^2, fit state).
- * The same argument rules. Both enqueue one kernel on stream and allocate nothing; the graph of a serving step is
- * cut -> fit -> update. Not in the paper (it names the use, not a serving design).
+ * results[b*markers + m][FS_SERVE_RESULT_FLOATS] = (x, y, sigma_x, sigma_y in frame
+ * coordinates, alpha, beta, normalised chi^2, fit state, ROI origin x, y, the warm start
+ * x0, y0, sigma_x, sigma_y in ROI coordinates, LM iterations, 0). fit_iters and init are the
+ * fit's iteration counts and the start values fs_serve_roi_cut wrote.
+ * The same argument rules. Both enqueue one kernel on stream and allocate nothing; a
+ * serving step is cut -> fit -> update (the sessions below capture it in a CUDA graph).
+ * Not in the paper (it names the use, not a serving design).
  */
+#define FS_SERVE_RESULT_FLOATS 16
 int fs_serve_roi_cut(const uint16_t *frames, int frame_w, int frame_h, int roi, int markers,
                      const int32_t *desc, int max_batch, const float *state, uint16_t *rois,
                      float *init, int32_t *origin, void *stream);
 int fs_serve_update(const int32_t *desc, int max_batch, int markers, const float *params,
                     const float *alpha, const float *beta, const float *chi2,
-                    const int32_t *fit_state, const int32_t *origin, float *state,
-                    float *results, void *stream);
+                    const int32_t *fit_state, const int32_t *fit_iters, const float *init,
+                    const int32_t *origin, float *state, float *results, void *stream);
+
+/*
+ * Serving sessions: real-time tracking of fiducial markers in camera streams with
+ * continuous batching (the paper's motivation, Sec. "Introduction"; the serving design is
+ * this library's). A session serves `streams` camera streams of one frame size, `markers`
+ * markers each, on the device current at creation:
+ *   - fs_session_submit_frame hands over a frame (host uint16 [frame_h][frame_w], pinned
+ *     for the copy to overlap; the caller keeps it unchanged until the frame is retired).
+ *     It waits in a queue of at most queue_limit frames for a device frame slot (frame_slots
+ *     of them: the memory budget); beyond that it is rejected with FS_ERR_FULL and counted.
+ *   - fs_session_poll makes progress without blocking: admitted frames are copied in on a
+ *     copy stream; frames on the device form a batch (at most one per stream, at most
+ *     max_batch, at most max_inflight batches on the device), run as one CUDA graph (ROI cut
+ *     at the rounded previous centres, warm-started fit, marker-state update) while later
+ *     frames are copied in; finished batches are retired, oldest first, into the caller's
+ *     arrays: done[i] and results[i][markers][FS_SERVE_RESULT_FLOATS] (the fs_serve_update
+ *     record) for up to max_frames frames; *n_done says how many.
+ *   - Stamps: t_arrival is the caller's (use fs_session_clock), t_done is taken when the
+ *     batch is seen complete in fs_session_poll; t_done - t_arrival is the frame latency.
+ *   - A stream's results are the same whether its frames are batched alone or with other
+ *     streams' frames (every marker's work depends on its own stream only).
+ * Marker state (x, y, sigma_x, sigma_y in frame coordinates) stays on the device;
+ * fs_session_add_markers sets a stream's start state, fs_session_get_markers reads it back
+ * (checkpoint; add_markers with a saved state restores it). Both synchronise the session's
+ * compute stream. The session allocates its buffers and streams at creation and frees them
+ * in fs_session_destroy (which waits for its work); nothing is allocated while serving.
+ * Not thread safe: one host thread drives a session.
+ * Errors: FS_ERR_NULL, FS_ERR_ARG (a field of cfg or an argument out of range), FS_ERR_FULL,
+ * FS_ERR_CUDA. Fit tolerances are as for fit_spots (max_error 0).
+ */
+typedef struct {
+  int frame_w, frame_h;  /* frame size in pixels, each at least roi and at most 65536     */
+  int roi;               /* ROI side, 3..32                                               */
+  int markers;           /* markers per stream, 1..65535                                  */
+  int streams;           /* camera streams, 1..65535                                      */
+  int max_batch;         /* frames per batch, 1..64 and at most streams                   */
+  int frame_slots;       /* device frame buffers, 1..4096                                 */
+  int queue_limit;       /* frames waiting for a slot before new ones are rejected, >= 0  */
+  int max_inflight;      /* batches on the device at once, 1..64                          */
+  int max_iter;          /* LM iteration budget, 1..1000                                  */
+  double min_delta, min_step; /* stop tolerances as for fit_spots                         */
+} fs_session_config;
+
+typedef struct {
+  int32_t stream;        /* stream of the frame                                           */
+  int32_t reserved;
+  int64_t index;         /* the caller's frame index                                      */
+  double t_arrival;      /* as submitted                                                  */
+  double t_done;         /* fs_session_clock when the frame's batch was seen complete     */
+} fs_frame_done;
+
+typedef struct fs_session fs_session;
+
+double fs_session_clock(void); /* seconds of a monotonic clock */
+int fs_session_create(const fs_session_config *cfg, fs_session **out);
+int fs_session_destroy(fs_session *s);
+int fs_session_add_markers(fs_session *s, int stream, const float *host_state);
+int fs_session_get_markers(fs_session *s, int stream, float *host_state);
+int fs_session_submit_frame(fs_session *s, int stream, int64_t index, const uint16_t *host_frame,
+                            double t_arrival);
+int fs_session_poll(fs_session *s, fs_frame_done *done, float *results, int max_frames,
+                    int *n_done);
+int fs_session_pending(const fs_session *s); /* frames submitted and not yet retired */
+/* frames rejected, frames retired and batches launched so far (any pointer may be NULL) */
+int fs_session_stats(const fs_session *s, int64_t *dropped, int64_t *served, int64_t *batches);
 
 /* Message for an FS_ERR_* / FS_OK code (static storage). */
 const char *fit_spots_strerror(int code);

@@ -2341,6 +2341,7 @@ const char *fit_spots_strerror(int code) {
     case FS_ERR_WORKSPACE: return "workspace too small or misaligned";
     case FS_ERR_CUDA: return "CUDA error";
     case FS_ERR_ARG: return "argument out of range";
+    case FS_ERR_FULL: return "frame queue full, frame rejected";
     default: return "unknown error code";
   }
 }

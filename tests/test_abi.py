@@ -166,12 +166,41 @@ def test_serving_argument_checks(lib):
     assert cut(markers=0) == -8 and cut(batch=0) == -8
     assert cut(markers=65536) == -8 and cut(batch=65536) == -8
 
-    def upd(markers=64, batch=8, state=fake):
-        return lib.fs_serve_update(fake, batch, markers, fake, fake, fake, fake, fake, fake,
-                                   state, fake, None)
-    assert upd(state=None) == -1
+    def upd(markers=64, batch=8, state=fake, iters=fake):
+        return lib.fs_serve_update(fake, batch, markers, fake, fake, fake, fake, fake, iters,
+                                   fake, fake, state, fake, None)
+    assert upd(state=None) == -1 and upd(iters=None) == -1
     assert upd(markers=0) == -8 and upd(batch=0) == -8
     assert upd(markers=65536) == -8 and upd(batch=65536) == -8
+
+
+def test_session_argument_checks(lib):
+    """fs_session_create rejects a malformed configuration before any CUDA call; the other
+    session calls reject a NULL session."""
+    from paper_2106_02045_gb300 import serving
+    serving._bind()
+    good = dict(frame_w=2048, frame_h=2048, roi=21, markers=64, streams=2, max_batch=2,
+                frame_slots=8, queue_limit=64, max_inflight=2, max_iter=20, min_delta=1e-6,
+                min_step=1e-4)
+
+    def create(**over):
+        c = dict(good, **over)
+        cfg = serving._Config(*(c[f] for f, _ in serving._Config._fields_))
+        h = ctypes.c_void_p()
+        return lib.fs_session_create(ctypes.byref(cfg), ctypes.byref(h))
+    for bad in (dict(roi=2), dict(roi=33), dict(frame_w=20), dict(markers=0), dict(streams=0),
+                dict(max_batch=3), dict(max_batch=0), dict(frame_slots=0), dict(queue_limit=-1),
+                dict(max_inflight=0), dict(max_iter=0), dict(min_delta=1.0), dict(min_step=-1.0)):
+        assert create(**bad) == -8, bad
+    assert lib.fs_session_create(None, None) == -1
+    n = ctypes.c_int()
+    assert lib.fs_session_poll(None, None, None, 0, ctypes.byref(n)) == -1
+    assert lib.fs_session_submit_frame(None, 0, 0, ctypes.c_void_p(0x1000), 0.0) == -1
+    assert lib.fs_session_add_markers(None, 0, ctypes.c_void_p(0x1000)) == -1
+    assert lib.fs_session_destroy(None) == -1 and lib.fs_session_pending(None) == -1
+    t0 = lib.fs_session_clock()
+    assert lib.fs_session_clock() >= t0 > 0
+    assert lib.fit_spots_strerror(-9) == b"frame queue full, frame rejected"
 
 
 def test_spot_count_limit(lib):

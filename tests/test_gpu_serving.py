@@ -1,12 +1,12 @@
-"""Serving loop: device ROI cut + warm-started fit + resident marker state, CUDA graphs,
-continuous batching across sessions, admission by memory, checkpoint / restore."""
-import time
-
+"""Serving sessions (fs_session_*): device ROI cut + warm-started fit + resident marker state,
+one CUDA graph per batch size, continuous batching across camera streams, admission by
+memory, checkpoint / restore, oracle parity of the served fits, real-time latency."""
 import numpy as np
 import pytest
 import torch
 
 from paper_2106_02045_gb300 import serving, synth
+from tests.parity import CONVERGED, REL_TOL, XY_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -26,11 +26,11 @@ def _stream(n_frames, markers, size, seed):
     return cs, host
 
 
-def _serve_alone(cs, host, markers, size, n):
-    srv = serving.TrackingServer(size, size, markers=markers, sessions=1, device=DEV)
+def _serve_alone(cs, host, markers, size, n, **kw):
+    srv = serving.TrackingServer(size, size, markers=markers, sessions=1, device=DEV, **kw)
     srv.set_markers(0, cs.start)
     for k in range(n):
-        srv.submit(0, k, host[k], time.perf_counter())
+        srv.submit(0, k, host[k], serving.clock())
         srv.drain()
     return srv
 
@@ -49,8 +49,43 @@ def test_tracker_follows_drifting_markers():
     assert np.median(err) < 0.03 and np.percentile(err, 99) < 0.15
 
 
+def test_served_fits_match_the_oracle():
+    """Every served marker fit, refitted by the FP64 oracle from the same ROI (cut on the host
+    at the origin the session reports) and the same warm start: centre within 1e-3 px, sigma,
+    alpha and beta within 1e-4 relative, the same convergence class."""
+    import oracle
+    markers, size, n, roi = 48, 640, 30, 21
+    cs, host = _stream(n, markers, size, seed=150)
+    srv = _serve_alone(cs, host, markers, size, n, roi=roi)
+    frames = host.view(torch.int16).numpy().view(np.uint16)
+    pix, init, res = [], [], []
+    for k in range(n):
+        r = srv.logs[0].results[k]                      # [markers, 16]
+        for m in range(markers):
+            ox, oy = int(r[m, 8]), int(r[m, 9])
+            pix.append(frames[k, oy:oy + roi, ox:ox + roi].ravel())
+            init.append(r[m, 10:14])
+            res.append(r[m])
+    res = np.array(res)
+    N = len(pix)
+    img = np.concatenate(pix).astype(np.uint16)
+    ref = oracle.fit_spots(img, np.arange(N, dtype=np.int64) * roi * roi,
+                           np.tile([roi, roi], (N, 1)), np.array(init, np.float32),
+                           np.zeros(N, np.uint8))
+    conv, rconv = np.isin(res[:, 7], CONVERGED), np.isin(ref["state"], CONVERGED)
+    both = conv & rconv
+    xy = np.abs(res[:, :2] - res[:, 8:10] - ref["params"][:, :2]).max(1)
+    rel = lambda a, b: np.abs(a - b) / np.abs(b)
+    ok = ((xy < XY_TOL) & (rel(res[:, 2], ref["params"][:, 2]) < REL_TOL) &
+          (rel(res[:, 4], ref["alpha"]) < REL_TOL) & (rel(res[:, 5], ref["beta"]) < REL_TOL))
+    print(f"served fits: {N}, class agreement {np.mean(conv == rconv):.5f}, "
+          f"within the bar {ok[both].mean():.5f}")
+    assert np.mean(conv == rconv) >= 0.999
+    assert ok[both].mean() >= 0.999
+
+
 def test_results_are_the_same_alone_and_in_the_mix():
-    """Session 0 served alone, then together with three other sessions whose frames arrive
+    """Stream 0 served alone, then together with three other streams whose frames arrive
     staggered and are batched with its frames: identical results, bit for bit."""
     markers, size, n = 24, 384, 24
     streams = [_stream(n, markers, size, seed=200 + s) for s in range(4)]
@@ -60,26 +95,19 @@ def test_results_are_the_same_alone_and_in_the_mix():
                                  queue_limit=1024, device=DEV)
     for s in range(4):
         srv.set_markers(s, streams[s][0].start)
-    # staggered arrivals: session s starts s rounds late; each round brings the next frame
-    # of every started session while earlier batches may still be on the device
-    sizes = []
-
-    def step():
-        n_before = len(srv.inflight)
-        srv.step()
-        if len(srv.inflight) > n_before:
-            sizes.append(len(srv.inflight[-1].frames))
+    # staggered arrivals: stream s starts s rounds late; each round brings the next frame
+    # of every started stream while earlier batches may still be on the device
     for r in range(n + 4):
         for s in range(4):
             k = r - s
             if 0 <= k < n:
-                srv.submit(s, k, streams[s][1][k], time.perf_counter())
+                srv.submit(s, k, streams[s][1][k], serving.clock())
         for _ in range(3):
-            step()
-    while srv.pending or srv.landed or srv.inflight:
-        step()
-    assert max(sizes) > 1                     # frames of different sessions shared batches
-    assert srv.dropped == 0
+            srv.step()
+    srv.drain()
+    st = srv.stats()
+    assert st["batches"] < st["served"]       # frames of different streams shared batches
+    assert st["dropped"] == 0 and st["served"] == 4 * n
     mixed = srv.logs[0].results
     for k in range(n):
         assert np.array_equal(alone[k].view(np.int32), mixed[k].view(np.int32)), k
@@ -93,34 +121,37 @@ def test_admission_rejects_beyond_queue_and_checkpoint_restores():
     srv = serving.TrackingServer(size, size, markers=markers, sessions=1, frame_slots=2,
                                  queue_limit=3, device=DEV)
     srv.set_markers(0, cs.start)
-    accepted = [srv.submit(0, k, host[k], time.perf_counter()) for k in range(n)]
+    accepted = [srv.submit(0, k, host[k], serving.clock()) for k in range(n)]
     assert sum(accepted) == 3 and srv.dropped == n - 3
     srv.drain()
     assert len(srv.logs[0].results) == 3
     # checkpoint, serve two frames, restore, serve them again: same results
     snap = srv.snapshot(0)
     for k in (3, 4):
-        srv.submit(0, k, host[k], time.perf_counter())
+        srv.submit(0, k, host[k], serving.clock())
         srv.drain()
     first = {k: srv.logs[0].results[k].copy() for k in (3, 4)}
     srv.restore(0, snap)
     for k in (3, 4):
-        srv.submit(0, k, host[k], time.perf_counter())
+        srv.submit(0, k, host[k], serving.clock())
         srv.drain()
     for k in (3, 4):
         assert np.array_equal(first[k], srv.logs[0].results[k])
 
 
-def test_realtime_stream_latency():
-    """2000 fps, 64 markers, 1024x1024 frames: every frame served, latency well below the
-    frame period at the median."""
-    markers, size, n = 64, 1024, 400
-    cs, host = _stream(64, markers, size, seed=400)
+def test_realtime_stream_latency_2048():
+    """The camera workload: 2048 x 2048 uint16 frames at 2000 fps, 64 markers, 21 x 21 ROIs,
+    20,000 frames after 1,000 warm-up frames: every frame served, the median latency (host
+    arrival stamp -> results on the host) inside the 0.5 ms frame period and the 99th
+    percentile within ten periods (the tail is host scheduling: 0.8 ms in a process of its
+    own, a few ms after the rest of the suite)."""
+    markers, size, ring, warm, n = 64, 2048, 128, 1000, 20000
+    cs, host = _stream(ring, markers, size, seed=400)
     srv = serving.TrackingServer(size, size, markers=markers, sessions=1, device=DEV)
     srv.set_markers(0, cs.start)
-    serving.run_stream(srv, 0, host, n, fps=2000.0)
-    lat = np.array([srv.logs[0].latency[k] for k in range(n)])
+    serving.run_stream(srv, 0, host, warm + n, fps=2000.0)
+    lat = np.array([srv.logs[0].latency[k] for k in range(warm, warm + n)])
     summ = serving.latency_summary(lat)
-    print("realtime 1024^2:", summ, "dropped", srv.dropped)
+    print("realtime 2048^2 at 2000 fps:", summ, "dropped", srv.dropped)
     assert srv.dropped == 0 and summ["frames"] == n
-    assert summ["p50_ms"] < 0.5
+    assert summ["p50_ms"] < 0.5 and summ["p99_ms"] < 5.0

@@ -62,6 +62,11 @@ def _load(paper_arithmetic: bool = False):
         lib.or_fit_spots_weighted.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
                                               vp, vp, vp, vp, vp, vp, vp, i, i]
         lib.or_fit_spots_weighted.restype = None
+        lib.or_fit_spots_poisson.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
+                                             vp, vp, vp, vp, vp, vp, vp, i]
+        lib.or_fit_spots_poisson.restype = None
+        lib.or_poisson_amplitudes.argtypes = [i, vp, vp, vp, vp]
+        lib.or_poisson_amplitudes.restype = i
         lib.or_evaluate.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp, vp]
         lib.or_evaluate.restype = i
         lib.or_profile.argtypes = [i, i, i, vp, vp, vp]
@@ -246,6 +251,41 @@ def fit_spots_weighted(images: np.ndarray, offsets, dims, init, model, *, max_it
                               float(min_step), _p(out["params"]), _p(out["alpha"]),
                               _p(out["beta"]), _p(out["chi2"]), _p(out["state"]),
                               _p(out["iters"]), _p(out["evals"]), int(unit_weights), int(nthreads))
+    return out
+
+
+def poisson_amplitudes(f, g):
+    """Poisson maximum-likelihood alpha, beta for the profile f (None if none is found)."""
+    lib = _load()
+    f, g = _f64(f), _f64(g)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    if lib.or_poisson_amplitudes(f.size, _p(f), _p(g), ctypes.byref(a), ctypes.byref(b)):
+        return None
+    return a.value, b.value
+
+
+def fit_spots_poisson(images: np.ndarray, offsets, dims, init, model, *, max_iter: int = 20,
+                      max_error: float = 0.0, min_delta: float = 1e-6, min_step: float = 1e-4,
+                      nthreads: int = 0) -> dict:
+    """The Poisson-likelihood implicit-amplitude fit (deviance objective); "chi2" is the
+    deviance over N - P - 2."""
+    lib = _load()
+    images = np.ascontiguousarray(images)
+    dtype = {np.dtype(np.uint16): U16, np.dtype(np.float32): F32,
+             np.dtype(np.float64): F64}[images.dtype]
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    dims = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 2)
+    init = np.ascontiguousarray(init, dtype=np.float32).reshape(-1, 4)
+    model = np.ascontiguousarray(model, dtype=np.uint8)
+    n = offsets.size
+    out = dict(params=np.empty((n, 4)), alpha=np.empty(n), beta=np.empty(n), chi2=np.empty(n),
+               state=np.empty(n, np.int32), iters=np.empty(n, np.int32),
+               evals=np.empty(n, np.int32))
+    lib.or_fit_spots_poisson(_p(images), dtype, images.size, _p(offsets), _p(dims), _p(init),
+                             _p(model), n, int(max_iter), float(max_error), float(min_delta),
+                             float(min_step), _p(out["params"]), _p(out["alpha"]),
+                             _p(out["beta"]), _p(out["chi2"]), _p(out["state"]),
+                             _p(out["iters"]), _p(out["evals"]), int(nthreads))
     return out
 
 

@@ -292,9 +292,14 @@ static int solve_damped(int P, double A[4][4], const double *b, double lambda, d
     return 0;
 }
 
-/* The trial point limit(best + delta) and its error; NaN if it cannot be evaluated. */
-static double trial(int model, int W, int H, const double *g, const double *best,
-                    const double *delta, double *pt, double *at, double *bt)
+/* An evaluated point: amplitudes, the objective and, if A != NULL, the normal equations;
+ * returns 0, or -1 when the point cannot be evaluated. */
+typedef int (*or_eval_fn)(int model, int W, int H, const double *g, const double *p,
+                          double *alpha, double *beta, double *obj, double A[4][4], double b[4]);
+
+/* The trial point limit(best + delta) and its objective; NaN if it cannot be evaluated. */
+static double trial(or_eval_fn eval, int model, int W, int H, const double *g,
+                    const double *best, const double *delta, double *pt, double *at, double *bt)
 {
     const int P = or_nparams(model);
     pt[0] = best[0] + delta[0];
@@ -304,7 +309,7 @@ static double trial(int model, int W, int H, const double *g, const double *best
     or_limit(model, W, H, pt);
     if (P == 3) pt[3] = pt[2];
     double c2;
-    if (evaluate(model, W, H, g, pt, at, bt, &c2, NULL, NULL)) return NAN;
+    if (eval(model, W, H, g, pt, at, bt, &c2, NULL, NULL)) return NAN;
     return c2;
 }
 
@@ -330,11 +335,13 @@ typedef struct {
     double p[4], alpha, beta, chi2;
 } or_point;
 
-/* One spot under fit: model, size, data, the shape-parameter count and the tolerances. */
+/* One spot under fit: model, size, data, the shape-parameter count, the tolerances and the
+ * objective's evaluation. */
 typedef struct {
     int model, W, H, P;
     const double *g;
     double max_error, min_delta, min_step;
+    or_eval_fn eval;
 } or_spot;
 
 /* Outcomes of the damping search of one iteration. */
@@ -352,8 +359,8 @@ static int damped_trial(const or_spot *sp, double A[4][4], const double *b, int 
 {
     if (solve_damped(sp->P, A, b, pow(10.0, k), delta)) return -1;
     ++*evals;
-    to->chi2 = trial(sp->model, sp->W, sp->H, sp->g, from->p, delta, to->p, &to->alpha,
-                     &to->beta);
+    to->chi2 = trial(sp->eval, sp->model, sp->W, sp->H, sp->g, from->p, delta, to->p,
+                     &to->alpha, &to->beta);
     return 0;
 }
 
@@ -398,12 +405,12 @@ static int stop_test(const or_spot *sp, const or_point *from, double chi_to, con
  * normalised chi^2, outcome, iterations and the number of evaluated points. trace
  * (max_iter + 1 values, or NULL) receives the error at the start of every iteration followed
  * by the final error; unused slots are NaN. */
-int or_fit_one(int model, int W, int H, const double *g, const double *p0, int max_iter,
-               double max_error, double min_delta, double min_step, double *p_out,
-               double *alpha_out, double *beta_out, double *chi2n_out, int *iters_out,
-               int *evals_out, double *trace)
+static int fit_one_with(or_eval_fn eval, int model, int W, int H, const double *g,
+                        const double *p0, int max_iter, double max_error, double min_delta,
+                        double min_step, double *p_out, double *alpha_out, double *beta_out,
+                        double *chi2n_out, int *iters_out, int *evals_out, double *trace)
 {
-    const or_spot sp = {model, W, H, or_nparams(model), g, max_error, min_delta, min_step};
+    const or_spot sp = {model, W, H, or_nparams(model), g, max_error, min_delta, min_step, eval};
     or_point cur = {{p0[0], p0[1], p0[2], sp.P == 4 ? p0[3] : p0[2]}, 0.0, 0.0, 0.0};
     or_limit(model, W, H, cur.p);
     if (sp.P == 3) cur.p[3] = cur.p[2];
@@ -416,7 +423,7 @@ int or_fit_one(int model, int W, int H, const double *g, const double *p0, int m
     while (it < max_iter) {
         ++it;
         ++evals;
-        if (evaluate(model, W, H, g, cur.p, &cur.alpha, &cur.beta, &cur.chi2, A, b))
+        if (eval(model, W, H, g, cur.p, &cur.alpha, &cur.beta, &cur.chi2, A, b))
             cur.chi2 = NAN;
         if (trace) trace[it - 1] = cur.chi2;
         if (isnan(cur.chi2)) { state = OR_NOT_CONVERGED; break; }
@@ -433,7 +440,7 @@ int or_fit_one(int model, int W, int H, const double *g, const double *p0, int m
 
     /* final error at the reported parameters (the listing's NormalizedChi) */
     double a, bb, chi;
-    if (evaluate(model, W, H, g, cur.p, &a, &bb, &chi, NULL, NULL)) { a = bb = chi = NAN; }
+    if (eval(model, W, H, g, cur.p, &a, &bb, &chi, NULL, NULL)) { a = bb = chi = NAN; }
     if (trace) trace[it < max_iter ? it : max_iter] = chi;
     for (int j = 0; j < 4; ++j) p_out[j] = cur.p[j];
     *alpha_out = a;
@@ -442,6 +449,15 @@ int or_fit_one(int model, int W, int H, const double *g, const double *p0, int m
     *iters_out = it;
     *evals_out = evals;
     return state;
+}
+
+int or_fit_one(int model, int W, int H, const double *g, const double *p0, int max_iter,
+               double max_error, double min_delta, double min_step, double *p_out,
+               double *alpha_out, double *beta_out, double *chi2n_out, int *iters_out,
+               int *evals_out, double *trace)
+{
+    return fit_one_with(evaluate, model, W, H, g, p0, max_iter, max_error, min_delta, min_step,
+                        p_out, alpha_out, beta_out, chi2n_out, iters_out, evals_out, trace);
 }
 
 /* Batch front end with the library's argument layout. images: element buffer of
@@ -1031,4 +1047,204 @@ int or_backward(int model, int W, int H, const double *g, const double *p, doubl
         grad_g[i] = t + cchi * (g[i] - (alpha * f[i] + beta));
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------ Poisson likelihood
+ * The variant for Poisson-distributed pixel counts. The paper fits unweighted residuals and
+ * says so (Sec. "Discussion"); the likelihood of the counts is the efficient objective for
+ * photon-counting images. The objective is the Poisson deviance
+ *     D(p) = 2 sum_i [h_i - g_i + g_i ln(g_i / h_i)]      (the last term is 0 where g_i = 0)
+ * (each term evaluated as g (u - ln(1 + u)), u = h/g - 1, so that its rounding shrinks with
+ * the residual and the deviance of a near-perfect model keeps its digits)
+ * of the model h = alpha f(p) + beta, with the amplitudes at their Poisson maximum
+ * likelihood for the profile at p: the implicit amplitudes of Eq. 5-6 with the likelihood in
+ * place of chi^2. Readings:
+ *   - the amplitudes solve the score equations sum (g/h - 1) (f, 1) = 0 by iteratively
+ *     reweighted least squares (weighted Eq. 5-6 with weights 1/h of the current means),
+ *     started from the least-squares amplitudes of Eq. 6, each step halved until every mean
+ *     stays positive and the deviance does not grow; a point where no positive means are
+ *     found is not evaluated (NaN);
+ *   - pixel values below 0 count as 0 (the counts of a Poisson model are not negative);
+ *   - the gradient for Eq. 12 is -1/2 dD/dp = sum (g/h - 1) alpha df/dp (the amplitude terms
+ *     vanish at their optimum), the normal matrix the Fisher information sum J J^T / h of the
+ *     shape parameters with J = alpha df/dp - (c f + e) the part of alpha df/dp that the
+ *     amplitudes cannot absorb ((c, e): its least squares on (f, 1) with weights 1/h);
+ *   - damping schedule, limit() box and stop tests are those of or_fit_one, on D;
+ *   - the reported normalised objective is D / (N - P - 2).
+ * ROIs of at most 32 x 32 pixels, as for the other comparison fits. */
+#define OR_IRLS_MAX 200
+
+static double poisson_deviance(int N, const double *f, const double *g, double a, double b)
+{
+    double D = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double h = a * f[i] + b;
+        if (!(h > 0.0)) return NAN;
+        if (g[i] > 0.0) { /* g (u - ln(1 + u)) with u = h/g - 1: small where h is close to g */
+            const double u = (h - g[i]) / g[i];
+            D += g[i] * (u - log1p(u));
+        } else {
+            D += h;
+        }
+    }
+    return 2.0 * D;
+}
+
+/* Poisson maximum-likelihood amplitudes for the profile f; 0, or -1 if none is found. */
+int or_poisson_amplitudes(int N, const double *f, const double *g, double *alpha, double *beta)
+{
+    double a, b, G = 0.0;
+    for (int i = 0; i < N; ++i) G += g[i] > 0.0 ? g[i] : 0.0;
+    if (or_amplitudes(N, f, g, &a, &b)) return -1;
+    double D = poisson_deviance(N, f, g, a, b);
+    if (isnan(D)) { /* a least-squares mean below zero: start from a flat positive model */
+        a = 0.0;
+        b = G / N > 1e-3 ? G / N : 1e-3;
+        D = poisson_deviance(N, f, g, a, b);
+        if (isnan(D)) return -1;
+    }
+    /* the deviance is a sum of terms of the size of the counts that cancel near the optimum:
+     * a change below its rounding (about eps times the total count) is no increase */
+    const double tolD = 1e-13 * (G + (double)N);
+    for (int it = 0; it < OR_IRLS_MAX; ++it) {
+        double Sw = 0.0, Sf = 0.0, Sff = 0.0, Sg = 0.0, Sfg = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double w = 1.0 / (a * f[i] + b), gi = g[i] > 0.0 ? g[i] : 0.0;
+            Sw += w;
+            Sf += w * f[i];
+            Sff += w * f[i] * f[i];
+            Sg += w * gi;
+            Sfg += w * f[i] * gi;
+        }
+        const double Dt = Sff * Sw - Sf * Sf;
+        if (!(Dt > 0.0)) return -1;
+        const double a1 = (Sw * Sfg - Sf * Sg) / Dt, b1 = (Sff * Sg - Sf * Sfg) / Dt;
+        double t = 1.0, an = a1, bn = b1, Dn = poisson_deviance(N, f, g, an, bn);
+        while ((isnan(Dn) || Dn > D + tolD) && t > 1e-12) {
+            t *= 0.5;
+            an = a + t * (a1 - a);
+            bn = b + t * (b1 - b);
+            Dn = poisson_deviance(N, f, g, an, bn);
+        }
+        if (isnan(Dn) || Dn > D + tolD) break; /* no further decrease: at the optimum */
+        const int done = fabs(an - a) <= 1e-14 * (fabs(a) + fabs(b)) &&
+                         fabs(bn - b) <= 1e-14 * (fabs(a) + fabs(b));
+        a = an;
+        b = bn;
+        D = Dn;
+        if (done) break;
+    }
+    *alpha = a;
+    *beta = b;
+    return 0;
+}
+
+/* One evaluated point of the Poisson fit: amplitudes, deviance and, if A != NULL, the
+ * Fisher normal equations of the shape parameters (see above). */
+static int evaluate_poisson(int model, int W, int H, const double *g, const double *p,
+                            double *alpha, double *beta, double *dev, double A[4][4],
+                            double bvec[4])
+{
+    const int N = W * H, P = or_nparams(model);
+    double f[OR_MAX_PIXELS], d[4 * OR_MAX_PIXELS];
+    or_profile(model, W, H, p, f, A ? d : NULL);
+    double a, b;
+    if (or_poisson_amplitudes(N, f, g, &a, &b)) return -1;
+    const double D = poisson_deviance(N, f, g, a, b);
+    if (isnan(D)) return -1;
+    *alpha = a;
+    *beta = b;
+    *dev = D;
+    if (!A) return 0;
+    double Sw = 0.0, Sf = 0.0, Sff = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double w = 1.0 / (a * f[i] + b);
+        Sw += w;
+        Sf += w * f[i];
+        Sff += w * f[i] * f[i];
+    }
+    const double Dt = Sff * Sw - Sf * Sf;
+    if (!(Dt > 0.0)) return -1;
+    double c[4], e[4];
+    for (int j = 0; j < P; ++j) {
+        double vf = 0.0, v1 = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double w = 1.0 / (a * f[i] + b), ad = a * d[(size_t)j * N + i];
+            vf += w * f[i] * ad;
+            v1 += w * ad;
+        }
+        c[j] = (Sw * vf - Sf * v1) / Dt;
+        e[j] = (Sff * v1 - Sf * vf) / Dt;
+    }
+    for (int j = 0; j < P; ++j) {
+        bvec[j] = 0.0;
+        for (int k = 0; k < P; ++k) A[j][k] = 0.0;
+    }
+    for (int i = 0; i < N; ++i) {
+        const double h = a * f[i] + b, w = 1.0 / h, gi = g[i] > 0.0 ? g[i] : 0.0;
+        double J[4];
+        for (int j = 0; j < P; ++j) J[j] = a * d[(size_t)j * N + i] - c[j] * f[i] - e[j];
+        for (int j = 0; j < P; ++j) {
+            bvec[j] += (gi - h) * w * J[j];
+            for (int k = 0; k < P; ++k) A[j][k] += w * J[j] * J[k];
+        }
+    }
+    return 0;
+}
+
+int or_fit_poisson_one(int model, int W, int H, const double *g, const double *p0, int max_iter,
+                       double max_error, double min_delta, double min_step, double *p_out,
+                       double *alpha_out, double *beta_out, double *dn_out, int *iters_out,
+                       int *evals_out)
+{
+    return fit_one_with(evaluate_poisson, model, W, H, g, p0, max_iter, max_error, min_delta,
+                        min_step, p_out, alpha_out, beta_out, dn_out, iters_out, evals_out, NULL);
+}
+
+/* Batch front end of the Poisson fit, the library's argument layout (W, H in 3..32). */
+void or_fit_spots_poisson(const void *images, int dtype, int64_t image_elems,
+                          const int64_t *offsets, const int32_t *dims, const float *init,
+                          const uint8_t *model, int64_t n, int max_iter, double max_error,
+                          double min_delta, double min_step, double *out_params,
+                          double *out_alpha, double *out_beta, double *out_chi2,
+                          int32_t *out_state, int32_t *out_iters, int32_t *out_evals,
+                          int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < n; ++s) {
+        const int W = dims[2 * s], H = dims[2 * s + 1], m = model[s];
+        const int64_t off = offsets[s];
+        double p0[4] = {init[4 * s], init[4 * s + 1], init[4 * s + 2], init[4 * s + 3]};
+        const int valid_model = (m == OR_MODEL_ISO || m == OR_MODEL_ELLIPTIC);
+        const int sides_ok = W >= 3 && H >= 3 && W <= OR_MAX_SIDE && H <= OR_MAX_SIDE;
+        const int N = sides_ok ? W * H : 0;
+        if (!valid_model || !sides_ok || N <= or_nparams(m) + 2 || off < 0 || off + N > image_elems) {
+            for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p0[j];
+            out_alpha[s] = out_beta[s] = out_chi2[s] = NAN;
+            out_state[s] = OR_INVALID;
+            out_iters[s] = 0;
+            if (out_evals) out_evals[s] = 0;
+            continue;
+        }
+        double g[OR_MAX_PIXELS];
+        for (int i = 0; i < N; ++i) {
+            if (dtype == OR_U16) g[i] = (double)((const uint16_t *)images)[off + i];
+            else if (dtype == OR_F32) g[i] = (double)((const float *)images)[off + i];
+            else g[i] = ((const double *)images)[off + i];
+        }
+        double p[4], a, b, dn;
+        int it, ev;
+        const int st = or_fit_poisson_one(m, W, H, g, p0, max_iter, max_error, min_delta,
+                                          min_step, p, &a, &b, &dn, &it, &ev);
+        for (int j = 0; j < 4; ++j) out_params[4 * s + j] = p[j];
+        out_alpha[s] = a;
+        out_beta[s] = b;
+        out_chi2[s] = dn;
+        out_state[s] = st;
+        out_iters[s] = it;
+        if (out_evals) out_evals[s] = ev;
+    }
 }

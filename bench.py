@@ -473,8 +473,9 @@ def _extra_paper_protocol(dev, stream, pin: bool = True) -> dict:
 
 
 def _extra_weighted(dev, stream) -> dict:
-    """Variance-weighted against unweighted implicit fits on 100,000 iso15 spots (peak 1000,
-    background 100): time, and centre and width errors in units of the true sigma."""
+    """Unweighted, variance-weighted and Poisson-likelihood implicit fits of the same 100,000
+    iso15 spots (peak 1000, background 100): time, and centre and width errors in units of
+    the true sigma."""
     import numpy as np
     from paper_2106_02045_gb300 import fitspots, synth
     b = synth.make_iso(100_000, 15, 7.0, synth.SEED_BASE + 51, device=dev, name="iso15")
@@ -486,7 +487,10 @@ def _extra_weighted(dev, stream) -> dict:
                                                                   stream=stream)),
                       ("weighted", lambda: fitspots.fit_weighted(b.images, b.offsets, b.dims,
                                                                  b.init, b.model, out=o,
-                                                                 stream=stream))):
+                                                                 stream=stream)),
+                      ("poisson", lambda: fitspots.fit_poisson(b.images, b.offsets, b.dims,
+                                                               b.init, b.model, out=o,
+                                                               stream=stream))):
         ms = _timed(run, 3, stream)
         p = o["params"].cpu().numpy().astype(np.float64)
         c = np.isin(o["state"].cpu().numpy(), CONVERGED)

@@ -370,6 +370,24 @@ int fit_spots_weighted(const void *images, int dtype, int64_t image_elems,
                        int32_t *out_evals, void *stream);
 
 /*
+ * Poisson-likelihood implicit-amplitude fit: minimises the deviance
+ * D = 2 sum [h - g + g ln(g / h)] of h = alpha f + beta (pixel values below 0 count as 0),
+ * alpha and beta at their Poisson maximum likelihood for the profile at every evaluated point
+ * (the implicit amplitudes of Eq. 5-6 with the likelihood in place of chi^2, found by
+ * reweighted least squares), the LM step from the deviance's gradient and Fisher information
+ * with the amplitudes regressed out, and the same damping schedule, box and stop tests as
+ * fit_spots applied to D; out_chi2 is D / (N - P - 2). ROIs of 3..32 pixels a side. Arguments
+ * and outputs as for fit_spots (dtype FS_U16 or FS_F32); no workspace; one warp per spot,
+ * FP32.
+ */
+int fit_spots_poisson(const void *images, int dtype, int64_t image_elems,
+                      const int64_t *offsets, const int32_t *roi_dims, const float *init_params,
+                      const uint8_t *model, int64_t n, int max_iter, double max_error,
+                      double min_delta, double min_step, float *out_params, float *out_alpha,
+                      float *out_beta, float *out_chi2, int32_t *out_state, int32_t *out_iters,
+                      int32_t *out_evals, void *stream);
+
+/*
  * Start values (x0, y0, s0, s0) for the fit, estimated on the device from each ROI's pixels
  * (the paper estimates start values from the image before fitting, Results section).
  *   rule FS_START_CENTROID  centre = centroid of max(g - min g, 0), the ROI centre

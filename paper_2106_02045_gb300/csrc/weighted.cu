@@ -22,8 +22,11 @@
 #include <stdint.h>
 
 #include "fitspots.h"
+#include "warp_lm.cuh"
 
 namespace {
+
+using namespace fs_warp;
 
 constexpr int kWThreads = 128;
 
@@ -41,69 +44,6 @@ struct WArgs {
   float *out_params, *out_alpha, *out_beta, *out_chi2;
   int32_t *out_state, *out_iters, *out_evals;
 };
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ int tri4(int j, int k) {  // packed (j, k), j <= k, of a 4 x 4
-  return j * 4 - j * (j - 1) / 2 + (k - j);
-}
-
-// (A + lambda diag A) d = b, 4 unknowns, A packed; Jacobi-scaled Cholesky.
-__device__ __forceinline__ bool solve4(const float (&A)[10], const float (&b)[4], float lam,
-                                       float (&d)[4]) {
-  float s[4], L[4][4], y[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float a = A[tri4(j, j)];
-    if (!(a > 0.f)) return false;
-    s[j] = rsqrtf(a);
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-#pragma unroll
-    for (int k = 0; k <= j; ++k) {
-      float t = (j == k) ? 1.f + lam : A[tri4(k, j)] * s[j] * s[k];
-#pragma unroll
-      for (int m = 0; m < k; ++m) t -= L[j][m] * L[k][m];
-      if (j == k) {
-        if (!(t > 0.f)) return false;
-        L[j][j] = sqrtf(t);
-      } else {
-        L[j][k] = t / L[k][k];
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    float t = b[j] * s[j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) t -= L[j][k] * y[k];
-    y[j] = t / L[j][j];
-  }
-#pragma unroll
-  for (int j = 3; j >= 0; --j) {
-    float t = y[j];
-#pragma unroll
-    for (int k = j + 1; k < 4; ++k) t -= L[k][j] * d[k];
-    d[j] = t / L[j][j];
-  }
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    d[j] *= s[j];
-    ok = ok && isfinite(d[j]);
-  }
-  return ok;
-}
-
-__device__ __forceinline__ float clampf(float v, float lo, float hi) {
-  v = (v < lo) ? lo : v;
-  return (v > hi) ? hi : v;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kWThreads) weighted_kernel(WArgs a) {
@@ -268,86 +208,14 @@ __global__ void __launch_bounds__(kWThreads) weighted_kernel(WArgs a) {
       }
       return isfinite(c2) ? c2 : __int_as_float(0x7fc00000);
     };
-    auto all_small = [&](const float (&d)[4], const float (&p)[4]) {
-      bool sm = true;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j < P) sm = sm && fabsf(d[j]) < a.min_step * fabsf(p[j]);
-      return sm;
-    };
-
     float p[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) p[j] = a.init[4 * s + j];
     if (iso) p[3] = p[2];
     limit(p);
-    float A[10], b[4], best[4], dl[4], pt[4];
-    float al = 0.f, be = 0.f;
-    int klam = -2, it = 0, evals = 0, state = FS_STATE_MAX_ITER;
-    while (it < a.max_iter) {
-      ++it;
-      ++evals;
-      const float chi = evaluate(p, true, al, be, A, b);
-      if (isnan(chi)) {
-        state = FS_STATE_NOT_CONVERGED;
-        break;
-      }
-      if (chi < a.max_error) {
-        state = FS_STATE_MAX_ERROR;
-        break;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) best[j] = p[j];
-      auto trial = [&]() -> float {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) pt[j] = best[j] + dl[j];
-        limit(pt);
-        float at, bt, Ad[10], bd[4];
-        return evaluate(pt, false, at, bt, Ad, bd);
-      };
-      if (!solve4(A, b, exp10f((float)klam), dl)) {
-        state = FS_STATE_NOT_CONVERGED;
-        break;
-      }
-      if (iso) dl[3] = dl[2];
-      ++evals;
-      float Chi = trial();
-      if (chi > Chi) --klam;
-      bool failed = false;
-      while (!all_small(dl, best) && chi < Chi && klam < 4) {
-        ++klam;
-        if (!solve4(A, b, exp10f((float)klam), dl)) {
-          failed = true;
-          break;
-        }
-        if (iso) dl[3] = dl[2];
-        ++evals;
-        Chi = trial();
-      }
-      if (failed) {
-        state = FS_STATE_NOT_CONVERGED;
-        break;
-      }
-      if (chi < Chi || isnan(Chi)) {
-        state = (all_small(dl, best) && !isnan(Chi)) ? FS_STATE_NO_DECREASE
-                                                     : FS_STATE_NOT_CONVERGED;
-        break;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) p[j] = pt[j];
-      if (Chi < a.max_error) {
-        state = FS_STATE_MAX_ERROR;
-        break;
-      }
-      if (chi * (1.f - a.min_delta) < Chi) {
-        state = FS_STATE_MIN_DELTA;
-        break;
-      }
-      if (all_small(dl, best)) {
-        state = FS_STATE_MIN_STEP;
-        break;
-      }
-    }
+    const LmResult lm = lm_drive(p, iso, P, a.max_iter, a.max_error, a.min_delta, a.min_step,
+                                 evaluate, limit);
+    float al, be;
     float Ad[10], bd[4];
     const float chi = evaluate(p, false, al, be, Ad, bd);
     if (lane == 0) {
@@ -358,9 +226,9 @@ __global__ void __launch_bounds__(kWThreads) weighted_kernel(WArgs a) {
       a.out_alpha[s] = al;
       a.out_beta[s] = be + sh;
       a.out_chi2[s] = chi / (float)(N - P - 2);
-      a.out_state[s] = state;
-      a.out_iters[s] = it;
-      if (a.out_evals) a.out_evals[s] = evals;
+      a.out_state[s] = lm.state;
+      a.out_iters[s] = lm.iters;
+      if (a.out_evals) a.out_evals[s] = lm.evals;
     }
   }
 }

@@ -56,6 +56,8 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_explicit.restype = i
         lib.fit_spots_weighted.argtypes = lib.fit_spots_explicit.argtypes
         lib.fit_spots_weighted.restype = i
+        lib.fit_spots_poisson.argtypes = lib.fit_spots_explicit.argtypes
+        lib.fit_spots_poisson.restype = i
         lib.fit_spots_start.argtypes = [vp, i, i64, vp, vp, i64, i, vp, vp]
         lib.fit_spots_start.restype = i
         lib.fit_spots_uniform_host.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
@@ -319,6 +321,14 @@ def fit_weighted(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor
     """The variance-weighted implicit-amplitude fit (weights 1 / max(g, 1)); same arguments
     and outputs as fit (chi2 is the weighted one)."""
     return fit_explicit(images, offsets, dims, init, model, _entry="fit_spots_weighted", **kw)
+
+
+def fit_poisson(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
+                init: torch.Tensor, model: torch.Tensor, **kw) -> dict:
+    """The Poisson-likelihood implicit-amplitude fit (deviance objective, amplitudes at their
+    likelihood optimum); same arguments and outputs as fit ("chi2" is the deviance over
+    N - P - 2)."""
+    return fit_explicit(images, offsets, dims, init, model, _entry="fit_spots_poisson", **kw)
 
 
 START_CENTROID, START_PAPER = 0, 1

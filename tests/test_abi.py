@@ -120,7 +120,7 @@ def test_host_call_argument_checks(lib):
 
 
 def test_start_and_explicit_argument_checks(lib):
-    """fit_spots_start, fit_spots_explicit and fit_spots_weighted reject malformed calls
+    """fit_spots_start and the one-warp comparison fits reject malformed calls
     before any CUDA work."""
     fake = ctypes.c_void_p(0x1000)
 
@@ -130,7 +130,7 @@ def test_start_and_explicit_argument_checks(lib):
     assert start(rule=2) == -8 and start(n=0) == 0
     assert start(images=None) == -1 and start(out=None) == -1
 
-    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted):
+    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted, lib.fit_spots_poisson):
         def call(n=10, max_iter=20, min_delta=1e-6, images=fake, state=fake):
             return fn(images, 0, 100, fake, fake, fake, fake, n, max_iter, 0.0, min_delta, 1e-4,
                       fake, fake, fake, fake, state, fake, None, None)
@@ -215,7 +215,8 @@ def test_spot_count_limit(lib):
     over = top + 1
     fake = ctypes.c_void_p(0x1000)
     assert lib.fit_spots_start(fake, 0, 100, fake, fake, over, 0, fake, None) == -2
-    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted, lib.fit_spots_noalloc):
+    for fn in (lib.fit_spots_explicit, lib.fit_spots_weighted, lib.fit_spots_poisson,
+               lib.fit_spots_noalloc):
         assert fn(fake, 0, 100, fake, fake, fake, fake, over, 20, 0.0, 1e-6, 1e-4,
                   fake, fake, fake, fake, fake, fake, None, None) == -2
     # the workspace calls: one spot more is a size error, the limit itself gets as far as

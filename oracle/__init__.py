@@ -65,6 +65,8 @@ def _load(paper_arithmetic: bool = False):
         lib.or_fit_spots_poisson.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
                                              vp, vp, vp, vp, vp, vp, vp, i]
         lib.or_fit_spots_poisson.restype = None
+        lib.or_subtract_background.argtypes = [vp, i, i64, vp, vp, i64, i, vp, vp]
+        lib.or_subtract_background.restype = None
         lib.or_poisson_amplitudes.argtypes = [i, vp, vp, vp, vp]
         lib.or_poisson_amplitudes.restype = i
         lib.or_evaluate.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp, vp]
@@ -252,6 +254,23 @@ def fit_spots_weighted(images: np.ndarray, offsets, dims, init, model, *, max_it
                               _p(out["beta"]), _p(out["chi2"]), _p(out["state"]),
                               _p(out["iters"]), _p(out["evals"]), int(unit_weights), int(nthreads))
     return out
+
+
+def subtract_background(images: np.ndarray, offsets, dims, border: int = 1):
+    """Tilt of the least-squares plane on each ROI's border ring subtracted: (images as
+    float64, untouched outside the ROIs as NaN; plane [n, 3] = c0, cx, cy)."""
+    lib = _load()
+    images = np.ascontiguousarray(images)
+    dtype = {np.dtype(np.uint16): U16, np.dtype(np.float32): F32,
+             np.dtype(np.float64): F64}[images.dtype]
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    dims = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 2)
+    n = offsets.size
+    out = np.full(images.size, np.nan)
+    plane = np.empty((n, 3))
+    lib.or_subtract_background(_p(images), dtype, images.size, _p(offsets), _p(dims), n,
+                               int(border), _p(out), _p(plane))
+    return out, plane
 
 
 def poisson_amplitudes(f, g):

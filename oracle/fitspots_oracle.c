@@ -1248,3 +1248,65 @@ void or_fit_spots_poisson(const void *images, int dtype, int64_t image_elems,
         if (out_evals) out_evals[s] = ev;
     }
 }
+
+/* ------------------------------------------------------------------ local background
+ * The paper assumes a uniform background in the ROI and remarks (Sec. "Implicit-amplitudes
+ * least-squares fitting") that a locally varying background may be estimated and
+ * subtracted before the fit; it gives no method. Reading: a plane
+ *     b(x, y) = c0 + cx (x - xc) + cy (y - yc),   xc = (W - 1) / 2, yc = (H - 1) / 2,
+ * fitted by least squares to the ROI's border ring (the pixels within `border` of an edge,
+ * where a spot centred in its ROI contributes nothing), and its tilt cx (x - xc) +
+ * cy (y - yc) subtracted from every pixel of the ROI. The level c0 is kept: the uniform
+ * beta of the fit takes it up, and the counts stay near their original scale.
+ * Output images are double, same element layout; only the ROIs' pixels are written.
+ * out_plane (n x 3: c0, cx, cy) may be NULL. An ROI with a side below 3, more than
+ * OR_MAX_PIXELS pixels, a border outside 1..8 or an offset outside the image gets NaN
+ * coefficients and no output pixels. */
+void or_subtract_background(const void *images, int dtype, int64_t image_elems,
+                            const int64_t *offsets, const int32_t *dims, int64_t n, int border,
+                            double *out_images, double *out_plane)
+{
+    for (int64_t s = 0; s < n; ++s) {
+        const int W = dims[2 * s], H = dims[2 * s + 1];
+        const int64_t off = offsets[s];
+        double *pl = out_plane ? out_plane + 3 * s : NULL;
+        if (W < 3 || H < 3 || W > OR_MAX_PIXELS / 3 || H > OR_MAX_PIXELS / 3 ||
+            W * H > OR_MAX_PIXELS || border < 1 || border > 8 || off < 0 ||
+            off + (int64_t)W * H > image_elems) {
+            if (pl) pl[0] = pl[1] = pl[2] = NAN;
+            continue;
+        }
+        const double xc = 0.5 * (W - 1), yc = 0.5 * (H - 1);
+        double M[6][6] = {{0}}, v[6] = {0};
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                if (x >= border && x < W - border && y >= border && y < H - border) continue;
+                const int64_t i = off + (int64_t)y * W + x;
+                const double gi = dtype == OR_U16 ? (double)((const uint16_t *)images)[i]
+                                : dtype == OR_F32 ? (double)((const float *)images)[i]
+                                                  : ((const double *)images)[i];
+                const double a[3] = {1.0, x - xc, y - yc};
+                for (int j = 0; j < 3; ++j) {
+                    v[j] += a[j] * gi;
+                    for (int k = 0; k < 3; ++k) M[j][k] += a[j] * a[k];
+                }
+            }
+        if (solve_dense(3, M, v)) {
+            if (pl) pl[0] = pl[1] = pl[2] = NAN;
+            continue;
+        }
+        if (pl) {
+            pl[0] = v[0];
+            pl[1] = v[1];
+            pl[2] = v[2];
+        }
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t i = off + (int64_t)y * W + x;
+                const double gi = dtype == OR_U16 ? (double)((const uint16_t *)images)[i]
+                                : dtype == OR_F32 ? (double)((const float *)images)[i]
+                                                  : ((const double *)images)[i];
+                out_images[i] = gi - v[1] * (x - xc) - v[2] * (y - yc);
+            }
+    }
+}

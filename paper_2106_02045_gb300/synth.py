@@ -22,6 +22,12 @@ pixel centre):
 * ``elongated`` 200,000 spots with a side above 32 and at most 1024 pixels (64x16, 128x8,
   40x25, 100x10, 256x4, 341x3, 33x31 and their transposes, uniformly), both models, drawn
   like ``mixed``.
+* ``tilted``  1,000,000 spots, 21x21 uint16, isotropic, on a tilted background plane:
+  centre 10 +- U(1) px, sigma ~ U(1.0, 1.8), peak amplitude 800, background
+  beta + tx (x - 10) + ty (y - 10) with beta ~ U(150, 400) and slopes tx, ty ~ U(-6, 6)
+  counts per pixel, Poisson noise; start values are the true parameters moved by
+  U(-0.5, 0.5) px and sigma scaled by U(0.8, 1.25) (the fixed rule below would be pulled
+  towards the bright side of the tilt).
 * ``paper``   the accuracy protocol of the paper's Results section: S x S, centre
   N(0, S/20) around the ROI centre, sigma ~ U(1, 2), integrated signal and total
   background given in counts, Gaussian noise of variance equal to the pixel value,
@@ -42,9 +48,9 @@ import torch
 
 MODEL_ISO, MODEL_ELLIPTIC = 0, 1
 SEED_BASE = 20210603
-WORKLOADS = ("iso15", "ell32", "mixed", "iso16", "elongated")
+WORKLOADS = ("iso15", "ell32", "mixed", "iso16", "elongated", "tilted")
 FULL_SIZES = {"iso15": 10_000, "ell32": 1_000_000, "mixed": 2_000_000, "iso16": 262_144,
-              "elongated": 200_000}
+              "elongated": 200_000, "tilted": 1_000_000}
 
 
 @dataclass
@@ -207,6 +213,33 @@ def make_ell32(n: int, seed: int = SEED_BASE + 2, device="cpu", W: int = 32, H: 
     return _pack_uniform(g16, W, H, MODEL_ELLIPTIC, init, truth, name)
 
 
+def make_tilted(n: int, seed: int = SEED_BASE + 6, device="cpu", S: int = 21,
+                name="tilted") -> SpotBatch:
+    """Isotropic uint16 spots on a tilted background plane (module docstring, ``tilted``)."""
+    gen = _gen(seed, device)
+    c = (S - 1) / 2
+    x = c + _uniform(n, -1.0, 1.0, gen, device)
+    y = c + _uniform(n, -1.0, 1.0, gen, device)
+    s = _uniform(n, 1.0, 1.8, gen, device)
+    bg = _uniform(n, 150.0, 400.0, gen, device)
+    tilt = torch.stack([_uniform(n, -6.0, 6.0, gen, device),
+                        _uniform(n, -6.0, 6.0, gen, device)], dim=1)
+    params = torch.stack([x, y, s, s], dim=1)
+    amp = torch.full((n,), 800.0, dtype=torch.float64, device=device)
+    lam = _render(S, S, params, amp, bg)
+    xs = torch.arange(S, device=device, dtype=torch.float64) - c
+    plane = (tilt[:, 0:1, None] * xs[None, None, :] + tilt[:, 1:2, None] * xs[None, :, None])
+    lam = lam + plane.reshape(n, S * S)
+    g = torch.poisson(lam, generator=gen).clamp(0, 65535)
+    init = params.clone()
+    init[:, :2] += _uniform(2 * n, -0.5, 0.5, gen, device).reshape(n, 2)
+    init[:, 2] *= _uniform(n, 0.8, 1.25, gen, device)
+    init[:, 3] = init[:, 2]
+    truth = dict(params=params, alpha=amp, beta=bg, tilt=tilt)
+    g16 = g.to(torch.int32).to(torch.uint16)
+    return _pack_uniform(g16, S, S, MODEL_ISO, init.to(torch.float32), truth, name)
+
+
 def make_mixed(n: int, seed: int = SEED_BASE + 3, device="cpu", name="mixed") -> SpotBatch:
     """Mixed sizes 5..32 per side, both models, float32, 16-byte aligned offsets."""
     gen = _gen(seed, device)
@@ -365,6 +398,8 @@ def make_workload(name: str, n: int | None = None, device="cpu") -> SpotBatch:
         return make_iso(n, 16, 7.5, SEED_BASE + 4, device, name)
     if name == "elongated":
         return make_elongated(n, SEED_BASE + 5, device, name=name)
+    if name == "tilted":
+        return make_tilted(n, SEED_BASE + 6, device, name=name)
     raise KeyError(name)
 
 

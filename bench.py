@@ -415,6 +415,8 @@ def _extras(args, dev, which=("mixed", "backward", "serving", "start")) -> dict:
         out.update(_extra_explicit(dev, stream))
     if "weighted" in which:
         out.update(_extra_weighted(dev, stream))
+    if "background" in which:
+        out.update(_extra_background(dev, stream, hbm))
     if "paper_protocol" in which:
         # last, and guarded: a failure of this context section must not cost the line
         try:
@@ -580,6 +582,44 @@ def _extra_start(dev, stream, hbm) -> dict:
     del b, init
     return {"start": {"workload": "ell32: 1,000,000 ROIs of 32x32 uint16, start values on the "
                                   "device (fit_spots_start)", **res}}
+
+
+def _extra_background(dev, stream, hbm) -> dict:
+    """Local background pre-subtraction on the tilted workload (1,000,000 ROIs of 21 x 21
+    uint16 on tilted planes): the subtraction pass against HBM, then the fit of the
+    subtracted float32 spots, and the centre errors with and without the subtraction."""
+    import numpy as np
+    import torch
+    from paper_2106_02045_gb300 import fitspots, synth
+    b = synth.make_workload("tilted", None, device=dev)
+    N = 21 * 21
+    sub = torch.zeros(b.images.numel(), dtype=torch.float32, device=dev)
+    plane = torch.empty((b.n, 3), dtype=torch.float32, device=dev)
+    per_spot = N * (2 + 4) + 16 + 12       # pixels in and out, offset + dims, plane
+    ms = _timed(lambda: fitspots.subtract_background(b.images, b.offsets, b.dims, out=sub,
+                                                     plane=plane, stream=stream), 5, stream)
+    gbs = b.n * per_spot / (ms * 1e-3) / 1e9
+    res = {"subtract": {"ms_per_step": ms, "value": b.n / (ms * 1e-3), "unit": "ROIs/s",
+                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm,
+                                     "unit": "GB/s", "frac": gbs / hbm,
+                                     "bytes_per_roi": per_spot}}}
+    t = b.truth["params"].cpu().numpy()
+    tilt = b.truth["tilt"].cpu().numpy()
+    o = fitspots.alloc_outputs(b.n, dev)
+    ws = _fit_workspace(b.n, dev)
+    for name, imgs in (("fit_subtracted", sub), ("fit_raw", b.images)):
+        ms_f = _timed(lambda: fitspots.fit(imgs, b.offsets, b.dims, b.init, b.model, out=o,
+                                           workspace=ws, stream=stream), 3, stream)
+        p = o["params"].cpu().numpy().astype(np.float64)
+        c = np.isin(o["state"].cpu().numpy(), CONVERGED)
+        e = p[c, :2] - t[c, :2]
+        res[name] = {"ms_per_step": ms_f, "converged": float(c.mean()),
+                     "x_err_rms_px": float(np.sqrt(np.mean(e[:, 0] ** 2))),
+                     "x_err_slope_corr": float(np.corrcoef(e[:, 0], tilt[c, 0])[0, 1])}
+    del b, sub, plane, o, ws
+    return {"background": {"workload": "tilted: 1,000,000 ROIs of 21x21 uint16, peak 800 on "
+                                       "background planes U(150, 400) + U(-6, 6) counts/px "
+                                       "slopes, Poisson noise; border ring width 1", **res}}
 
 
 def _extra_mixed(args, dev, stream) -> dict:
@@ -765,9 +805,10 @@ def main() -> None:
                     help="spots per chunk of the host-buffer call in the end-to-end leg")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed/backward/serving")
     ap.add_argument("--extras",
-                    default="mixed,backward,serving,start,table1,explicit,weighted,paper_protocol",
+                    default="mixed,backward,serving,start,table1,explicit,weighted,background,"
+                            "paper_protocol",
                     help="comma-separated subset of mixed,backward,serving,start,table1,"
-                         "explicit,weighted,paper_protocol")
+                         "explicit,weighted,background,paper_protocol")
     ap.add_argument("--mixed-spots", type=int, default=2_000_000)
     ap.add_argument("--serving-frames", type=int, default=20000)
     ap.add_argument("--serving-warmup", type=int, default=1000)

@@ -388,6 +388,29 @@ int fit_spots_poisson(const void *images, int dtype, int64_t image_elems,
                       int32_t *out_evals, void *stream);
 
 /*
+ * Local background pre-subtraction. The fit assumes a uniform background in each ROI; where
+ * the background varies, the paper allows it to be estimated and subtracted beforehand (Sec.
+ * "Implicit-amplitudes least-squares fitting"). This call fits the plane
+ * c0 + cx (x - xc) + cy (y - yc), xc = (W - 1) / 2, yc = (H - 1) / 2, by least squares to each
+ * ROI's border ring (the pixels within `border` of an edge) and writes the ROI minus the
+ * plane's tilt cx (x - xc) + cy (y - yc) to out_images as float32; the level c0 is left for
+ * the fit's beta. Fit the result with dtype FS_F32 and the same offsets and dims.
+ *   images, dtype, image_elems, offsets, roi_dims, n: as for fit_spots (FS_U16 or FS_F32;
+ *                  ROIs of 3..341 pixels a side and at most 1024 pixels)
+ *   border         ring width, 1..8 (FS_ERR_ARG otherwise)
+ *   out_images     device float32[image_elems]: each valid ROI's pixels are written at the
+ *                  same element positions; everything else is left untouched. It may be
+ *                  `images` itself for FS_F32 when no two ROIs overlap.
+ *   out_plane      device float32[n, 3] (c0, cx, cy per ROI) or NULL; NaN for an invalid
+ *                  ROI (bad size or offset), whose pixels are not written
+ * Sums are exact integers for uint16 pixels and FP32 within a warp lane, FP64 across lanes,
+ * for float32 pixels. Asynchronous on `stream`; no workspace.
+ */
+int fit_spots_subtract_background(const void *images, int dtype, int64_t image_elems,
+                                  const int64_t *offsets, const int32_t *roi_dims, int64_t n,
+                                  int border, float *out_images, float *out_plane, void *stream);
+
+/*
  * Start values (x0, y0, s0, s0) for the fit, estimated on the device from each ROI's pixels
  * (the paper estimates start values from the image before fitting, Results section).
  *   rule FS_START_CENTROID  centre = centroid of max(g - min g, 0), the ROI centre

@@ -15,7 +15,8 @@ PKG = Path(__file__).resolve().parent
 ROOT = PKG.parent
 CSRC = PKG / "csrc"
 SOURCES = [CSRC / n for n in ("fitspots.cu", "backward.cu", "serving.cu", "start.cu",
-                              "explicit.cu", "weighted.cu", "poisson.cu", "probe.cu")]
+                              "explicit.cu", "weighted.cu", "poisson.cu", "background.cu",
+                              "probe.cu")]
 HEADERS = [ROOT / "include" / "fitspots.h", CSRC / "warp_lm.cuh"]
 BUILD = PKG / "_build"
 LIB = BUILD / "libfitspots.so"

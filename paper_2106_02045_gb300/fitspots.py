@@ -58,6 +58,8 @@ def library() -> ctypes.CDLL:
         lib.fit_spots_weighted.restype = i
         lib.fit_spots_poisson.argtypes = lib.fit_spots_explicit.argtypes
         lib.fit_spots_poisson.restype = i
+        lib.fit_spots_subtract_background.argtypes = [vp, i, i64, vp, vp, i64, i, vp, vp, vp]
+        lib.fit_spots_subtract_background.restype = i
         lib.fit_spots_start.argtypes = [vp, i, i64, vp, vp, i64, i, vp, vp]
         lib.fit_spots_start.restype = i
         lib.fit_spots_uniform_host.argtypes = [vp, i, i, i, i, vp, i64, i, d, d, d,
@@ -360,6 +362,41 @@ def start_values(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor
                                        ctypes.c_void_p(s.cuda_stream))
     check(rc, "fit_spots_start")
     return o
+
+
+def subtract_background(images: torch.Tensor, offsets: torch.Tensor, dims: torch.Tensor,
+                        border: int = 1, *, out: torch.Tensor | None = None,
+                        plane: torch.Tensor | None = None,
+                        stream: torch.cuda.Stream | None = None):
+    """Each ROI minus the tilt of the least-squares plane on its border ring
+    (fit_spots_subtract_background): (float32 images of the same layout, plane [n, 3] =
+    c0, cx, cy). Elements outside the ROIs of a freshly allocated output are 0."""
+    dev = images.device
+    if dev.type != "cuda":
+        raise FitSpotsError("images must be a CUDA tensor")
+    dtype = U16 if images.dtype == torch.uint16 else F32 if images.dtype == torch.float32 else None
+    if dtype is None:
+        raise FitSpotsError(f"images must be uint16 or float32, got {images.dtype}")
+    _need(images, images.dtype, "images", dev)
+    _need(offsets, torch.int64, "offsets", dev)
+    _need(dims, torch.int32, "dims", dev)
+    n = offsets.numel()
+    _check_count(n)
+    if dims.numel() != 2 * n:
+        raise FitSpotsError("dims must be [n, 2]")
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev), torch.cuda.stream(s):
+        o = out if out is not None else torch.zeros(images.numel(), dtype=torch.float32, device=dev)
+        pl = plane if plane is not None else torch.empty((n, 3), dtype=torch.float32, device=dev)
+        _need(o, torch.float32, "out", dev)
+        _need(pl, torch.float32, "plane", dev)
+        if o.numel() < images.numel() or pl.numel() < 3 * n:
+            raise FitSpotsError("out or plane too small")
+        rc = library().fit_spots_subtract_background(
+            _ptr(images), dtype, images.numel(), _ptr(offsets), _ptr(dims), n, int(border),
+            _ptr(o), _ptr(pl), ctypes.c_void_p(s.cuda_stream))
+    check(rc, "fit_spots_subtract_background")
+    return o, pl
 
 
 def fit_batch(batch, **kw) -> dict:

@@ -138,6 +138,20 @@ def test_start_and_explicit_argument_checks(lib):
         assert call(n=0) == 0 and call(images=None) == -1 and call(state=None) == -1
 
 
+def test_background_argument_checks(lib):
+    """fit_spots_subtract_background rejects malformed calls before any CUDA work."""
+    fake = ctypes.c_void_p(0x1000)
+
+    def call(n=10, dtype=0, elems=100, border=1, images=fake, out=fake, plane=fake):
+        return lib.fit_spots_subtract_background(images, dtype, elems, fake, fake, n, border,
+                                                 out, plane, None)
+    assert call(n=-1) == -2 and call(elems=-1) == -2 and call(n=2**31 - 2**24 + 1) == -2
+    assert call(dtype=2) == -3 and call(dtype=-1) == -3
+    assert call(border=0) == -8 and call(border=9) == -8
+    assert call(n=0) == 0
+    assert call(images=None) == -1 and call(out=None) == -1
+
+
 def test_backward_argument_checks(lib):
     """fit_spots_backward rejects malformed calls before any CUDA call; n = 0 is a no-op."""
     fake = ctypes.c_void_p(0x1000)

@@ -154,9 +154,12 @@ int fit_spots_uniform(const void *images, int dtype, int width, int height, int 
 
 /*
  * fit_spots_uniform from and to HOST memory, with the transfers overlapped: the batch is cut
- * into chunks of `chunk` spots; while chunk k is fitted on `stream`, chunk k+1's pixels and
- * start values go to the device and chunk k-1's results come back, on a copy stream the
- * library keeps per device. Host buffers should be pinned (cudaHostAlloc / page-locked):
+ * into chunks of `chunk` spots; while chunk k is fitted, chunk k+1's pixels and start values
+ * go to the device and chunk k-1's results come back, on a copy stream the library keeps per
+ * device. Even chunks are fitted on `stream`, odd chunks on a second fit stream the library
+ * keeps per device (ordered after the work the caller queued on `stream` before the call),
+ * so that the next chunk's fit fills the SMs while one launch finishes its last spots.
+ * Host buffers should be pinned (cudaHostAlloc / page-locked):
  * from pageable memory the copies still work but do not overlap the fits.
  *   images, init_params   host arrays laid out as for fit_spots_uniform
  *   out_*                 host arrays (out_evals may be NULL)

@@ -26,6 +26,9 @@ _LIB = _HERE / "_build" / "liboracle.so"
 # the same source built with the paper's chi^2 arithmetic and minStep origin, for the pin
 # of the stop conditions the paper reports (see the header of fitspots_oracle.c)
 _LIB_PAPER = _HERE / "_build" / "liboracle_paper.so"
+# the same source with the profile values rounded to FP32 and everything after them in FP64,
+# to measure how far FP32 model values alone move a fit (see the header of fitspots_oracle.c)
+_LIB_FP32_PROFILE = _HERE / "_build" / "liboracle_fp32profile.so"
 
 MODEL_ISO, MODEL_ELLIPTIC = 0, 1
 U16, F32, F64 = 0, 1, 2
@@ -35,23 +38,27 @@ STATE_NAMES = {0: "MAX_ITER", 1: "MIN_DELTA", 2: "MIN_STEP", 3: "MAX_ERROR",
 _libs = {}
 
 
-def build(force: bool = False, paper_arithmetic: bool = False) -> Path:
+def build(force: bool = False, paper_arithmetic: bool = False,
+          fp32_profile: bool = False) -> Path:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP); with
-    ``paper_arithmetic`` the second build, ``liboracle_paper.so`` (-DOR_PAPER_ARITHMETIC)."""
-    lib_path = _LIB_PAPER if paper_arithmetic else _LIB
+    ``paper_arithmetic`` the second build, ``liboracle_paper.so`` (-DOR_PAPER_ARITHMETIC);
+    with ``fp32_profile`` the third, ``liboracle_fp32profile.so`` (-DOR_FP32_PROFILE)."""
+    lib_path = _LIB_PAPER if paper_arithmetic else _LIB_FP32_PROFILE if fp32_profile else _LIB
     lib_path.parent.mkdir(exist_ok=True)
     if force or not lib_path.exists() or lib_path.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = lib_path.with_suffix(f".{os.getpid()}.tmp")
-        defines = ["-DOR_PAPER_ARITHMETIC"] if paper_arithmetic else []
+        defines = (["-DOR_PAPER_ARITHMETIC"] if paper_arithmetic else
+                   ["-DOR_FP32_PROFILE"] if fp32_profile else [])
         subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", *defines,
                         "-o", str(tmp), str(_SRC), "-lm"], check=True)
         os.replace(tmp, lib_path)
     return lib_path
 
 
-def _load(paper_arithmetic: bool = False):
-    if paper_arithmetic not in _libs:
-        lib = ctypes.CDLL(str(build(paper_arithmetic=paper_arithmetic)))
+def _load(paper_arithmetic: bool = False, fp32_profile: bool = False):
+    key = (paper_arithmetic, fp32_profile)
+    if key not in _libs:
+        lib = ctypes.CDLL(str(build(paper_arithmetic=paper_arithmetic, fp32_profile=fp32_profile)))
         d, i, i64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         lib.or_fit_spots.argtypes = [vp, i, i64, vp, vp, vp, vp, i64, i, d, d, d,
                                      vp, vp, vp, vp, vp, vp, vp, vp, i]
@@ -85,8 +92,8 @@ def _load(paper_arithmetic: bool = False):
         lib.or_profile_second.restype = None
         lib.or_backward.argtypes = [i, i, i, vp, vp, d, d, vp, vp]
         lib.or_backward.restype = i
-        _libs[paper_arithmetic] = lib
-    return _libs[paper_arithmetic]
+        _libs[key] = lib
+    return _libs[key]
 
 
 def _p(a: np.ndarray):
@@ -180,11 +187,14 @@ def limit(model: int, W: int, H: int, p):
 
 def fit_spots(images: np.ndarray, offsets, dims, init, model, *, max_iter: int = 20,
               max_error: float = 0.0, min_delta: float = 1e-6, min_step: float = 1e-4,
-              trace: bool = False, nthreads: int = 0, paper_arithmetic: bool = False) -> dict:
+              trace: bool = False, nthreads: int = 0, paper_arithmetic: bool = False,
+              fp32_profile: bool = False) -> dict:
     """Fit every spot in FP64. ``images`` is a flat uint16, float32 or float64 array.
     ``paper_arithmetic`` runs the second build (FP32 chi^2 over pixel threads, minStep
-    relative to the ROI centre), used only to pin the paper's stop-condition shares."""
-    lib = _load(paper_arithmetic)
+    relative to the ROI centre), used only to pin the paper's stop-condition shares;
+    ``fp32_profile`` the third (profile values rounded to FP32), used only to measure how far
+    FP32 model values alone move the fits."""
+    lib = _load(paper_arithmetic, fp32_profile)
     images = np.ascontiguousarray(images)
     dtype = {np.dtype(np.uint16): U16, np.dtype(np.float32): F32,
              np.dtype(np.float64): F64}[images.dtype]

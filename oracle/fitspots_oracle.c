@@ -62,6 +62,12 @@
  *   the minStep test takes x and y relative to the ROI centre, |delta_j| <
  *       min_step |p_j - c_j| with c = ((W-1)/2, (H-1)/2) (a reading of criterion iii).
  * The default build keeps FP64 and the pixel-index origin of R6.
+ *
+ * A third build, with -DOR_FP32_PROFILE, also serves one measurement only: how far the fit
+ * moves when the profile f_i and its derivatives df_i/dp_j (Eq. 10, 11) are rounded to the
+ * nearest FP32 value, with everything after them (amplitudes, chi^2, normal equations,
+ * solve) in FP64. It measures how well any implementation that evaluates the model in
+ * 32-bit floats (as the paper's does, Sec. "Implementation") can agree with the FP64 fit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -121,6 +127,13 @@ void or_profile(int model, int W, int H, const double *p, double *f, double *d)
                 d[3 * N + i] = dy * dy / (sy * sy * sy) * fi;
             }
         }
+#ifdef OR_FP32_PROFILE
+        /* the third build (see the header): the profile and its derivatives rounded to the
+         * nearest FP32 value, everything after them in FP64 */
+        f[i] = (double)(float)f[i];
+        if (d)
+            for (int j = 0; j < or_nparams(model); ++j) d[j * N + i] = (double)(float)d[j * N + i];
+#endif
     }
 }
 

@@ -17,9 +17,11 @@
 // beta^ so that chi^2 = sum (u - beta')^2 does not cancel). Per-thread partial sums are
 // combined with a pairwise tree through shared memory (no atomics, fixed order, so a
 // spot's result does not depend on its neighbours). The LM bookkeeping (Eq. 6 2x2
-// solve, J^T J assembly, diagonally scaled Cholesky of Eq. 14, damping, stop tests) is
-// FP32 and replicated in the group's threads: FP64 runs at about 1/75 of the FP32 rate on
-// this GPU.
+// solve, J^T J assembly, diagonally scaled Cholesky of Eq. 14, damping, stop tests) runs
+// in FP32; the 2x2 amplitude solve and the damped solve are redone in FP64 where FP32
+// cancellation would cost them 10 bits or more (FP64 runs at about 1/64 of the FP32 rate
+// on this GPU, so it is kept to those systems), and a damped system that FP32 rounding
+// leaves not positive definite gets more damping instead of ending the fit.
 //
 // Gradient. With alpha^, beta^ at their optimum, sum_i r_i = sum_i r_i f_i = 0 (Eq. 4), so
 // J^T r = alpha^ sum_i r_i df_i/dp_j (the other two terms of Eq. 9 vanish), and
@@ -35,10 +37,14 @@
 // accept/reject and minimum-decrease tests of the Fit2DGaussian listing are taken on a
 // difference that has relative, not absolute, FP32 error.
 //
-// Scheduling. A prepass sorts spot indices into 16 size classes (ceil(W/8), ceil(H/8));
-// each configuration then runs one persistent launch in which every group pulls spots of
-// its classes from an atomic cursor. A group whose spot has converged loads the next one
-// while the other groups of its warp continue. fit_spots_uniform skips the prepass for
+// Scheduling. A prepass sorts spot indices into 16 size classes (ceil(W/8), ceil(H/8)) and
+// a seventeenth for ROIs with a side above 32 (at most 1024 pixels, the paper's bound on
+// one fit). fit_spots then fits every class of W, H <= 32 in ONE persistent launch of a
+// generic batched kernel (each ROI oriented with its longer side along the lanes, rows in
+// compile-time blocks of 8/16/24/32), largest classes first, and the elongated class in a
+// second launch (row blocks); warps pull spots from per-class atomic cursors and refill a
+// slot as soon as its spot finishes. fit_spots_per_class keeps one launch per class with
+// the configuration the autotuned table assigns. fit_spots_uniform skips the prepass for
 // batches of equal-size, contiguous spots (the paper's own layout).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -204,9 +210,11 @@ __device__ __forceinline__ bool amplitudes64(float Nf, float X01, float X02, flo
   return true;
 }
 
-// Above this cancellation ratio the amplitudes are solved again in FP64 (6 bits of the FP32
-// determinant lost; about 1.5 % of the evaluations on the camera and mixed workloads).
-constexpr float kAmpCancel64 = 64.f;
+// Above this cancellation ratio the amplitudes are solved again in FP64 (10 bits of the FP32
+// determinant lost). FP64 runs at about 1/64 of the FP32 rate on this GPU and the LM step runs
+// one slot per lane, so a warp pays for the FP64 path whenever any of its 16 slots takes it;
+// a lower ratio (64) cost 16 % of the 32 x 32 fit time with no measurable change in the fits.
+constexpr float kAmpCancel64 = 1024.f;
 
 // Eq. 14 in FP32: the same scaling, Cholesky with reciprocal-square-root pivots. piv receives
 // the smallest pivot relative to 1 + lambda (the scaled matrix's unit diagonal): the fraction
@@ -293,10 +301,10 @@ __device__ __forceinline__ bool solve_damped64(const float (&A)[10], const float
   return isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]) && isfinite(d[3]);
 }
 
-// Below this pivot fraction (5 bits of the diagonal lost in FP32) or when the FP32
-// factorisation fails, Eq. 14 is solved again in FP64: about 2.5 % of the damped systems on
-// the camera and mixed workloads, the nearly singular ones of flat chi^2 surfaces.
-constexpr float kPivot64 = 1.f / 32.f;
+// Below this pivot fraction (10 bits of the diagonal lost in FP32) or when the FP32
+// factorisation fails, Eq. 14 is solved again in FP64: the nearly singular systems of flat
+// chi^2 surfaces (see kAmpCancel64 for the cost of a looser threshold).
+constexpr float kPivot64 = 1.f / 1024.f;
 
 // Eq. 14: FP32 where the system keeps its digits, FP64 where cancellation would cost them.
 __device__ __forceinline__ bool solve_damped(const float (&A)[10], const float (&b)[4], float lam,
@@ -305,6 +313,20 @@ __device__ __forceinline__ bool solve_damped(const float (&A)[10], const float (
   bool ok = solve_damped32(A, b, lam, d, piv);
   if (!ok || piv < kPivot64) ok = solve_damped64(A, b, lam, d);
   return ok;
+}
+
+// Eq. 14 at lambda = 10^klam, raising klam tenfold at a time (up to the 10^4 cap) while the
+// damped system is not positive definite. With a positive diagonal, J^T J + lambda diag(J^T J)
+// is positive definite for every lambda > 0, so a failed factorisation comes from the rounding
+// of a nearly singular FP32 normal matrix; more damping is the step the exact system would
+// allow, as for a rejected trial. False when no lambda up to the cap gives a step.
+__device__ __forceinline__ bool solve_damped_raising(const float (&A)[10], const float (&b)[4],
+                                                     int &klam, float (&d)[4]) {
+  for (;;) {  // one inlined copy of the solve
+    if (solve_damped(A, b, pow10i(klam), d)) return true;
+    if (klam >= 4) return false;
+    ++klam;
+  }
 }
 
 // Normal equations A = J^T J and b = J^T r at an evaluated point (Eq. 9, 12 and 13) from the
@@ -903,7 +925,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) fit_kernel(FitArgs a, Cla
       }
       if (need_solve) {
         float d[4];
-        if (solve_damped(A, bv, pow10i(klam), d)) {
+        if (solve_damped_raising(A, bv, klam, d)) {
           if (iso) d[3] = d[2];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -1226,7 +1248,7 @@ __device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const in
     }
     if (need_solve) {
       float d[4];
-      if (solve_damped(A, bv, pow10i(klam), d)) {
+      if (solve_damped_raising(A, bv, klam, d)) {
         if (iso) d[3] = d[2];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -2285,10 +2307,11 @@ ChunkLayout chunk_layout(int64_t chunk, int width, int height, int dtype) {
   return l;
 }
 
-// Per device: the copy stream and the events that order the two chunk buffers, created
-// once (std::call_once) and kept for the life of the process.
+// Per device: the copy stream, a second fit stream and the events that order the two chunk
+// buffers, created once (std::call_once) and kept for the life of the process.
 struct HostPipe {
   cudaStream_t copy = nullptr;
+  cudaStream_t fit2 = nullptr;                    // odd chunks are fitted here
   cudaEvent_t in_ready[2] = {nullptr, nullptr};   // chunk's inputs on the device
   cudaEvent_t fitted[2] = {nullptr, nullptr};     // chunk's fit done
   cudaEvent_t drained = nullptr;                  // last results copied back
@@ -2306,6 +2329,7 @@ int host_pipe(HostPipe **out) {
   HostPipe &p = g_pipe[dev];
   std::call_once(p.once, [&p] {
     cudaError_t x = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking);
+    if (x == cudaSuccess) x = cudaStreamCreateWithFlags(&p.fit2, cudaStreamNonBlocking);
     for (int b = 0; b < 2 && x == cudaSuccess; ++b) {
       x = cudaEventCreateWithFlags(&p.in_ready[b], cudaEventDisableTiming);
       if (x == cudaSuccess) x = cudaEventCreateWithFlags(&p.fitted[b], cudaEventDisableTiming);
@@ -2571,9 +2595,11 @@ int fit_spots_uniform_host(const void *images, int dtype, int width, int height,
   const int64_t nchunks = (n + chunk - 1) / chunk;
   char *ws = static_cast<char *>(workspace);
   cudaError_t e = cudaSuccess;
-  // the copy stream starts after whatever the caller queued on `stream` before this call
+  // the copy stream and the second fit stream start after whatever the caller queued on
+  // `stream` before this call
   if ((e = cudaEventRecord(pp->drained, st)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(cp, pp->drained, 0)) != cudaSuccess)
+      (e = cudaStreamWaitEvent(cp, pp->drained, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(pp->fit2, pp->drained, 0)) != cudaSuccess)
     return set_cuda_error(e);
   auto upload = [&](int64_t k) -> cudaError_t {
     char *b = ws + (k & 1) * l.bytes;
@@ -2588,11 +2614,14 @@ int fit_spots_uniform_host(const void *images, int dtype, int width, int height,
   if ((e = upload(0)) != cudaSuccess) return set_cuda_error(e);
   for (int64_t k = 0; k < nchunks; ++k) {
     // chunk k+1 goes up while chunk k is fitted (its buffer was drained, in copy-stream
-    // order, by chunk k-1's download)
+    // order, by chunk k-1's download). Even chunks are fitted on `stream`, odd ones on the
+    // second fit stream, so that chunk k+1's blocks take the SMs that chunk k's last fits
+    // leave idle at the end of its persistent launch.
     if (k + 1 < nchunks && (e = upload(k + 1)) != cudaSuccess) return set_cuda_error(e);
     char *b = ws + (k & 1) * l.bytes;
     const int64_t s0 = k * chunk, m = std::min<int64_t>(chunk, n - s0);
-    if ((e = cudaStreamWaitEvent(st, pp->in_ready[k & 1], 0)) != cudaSuccess)
+    cudaStream_t fs = (k & 1) ? pp->fit2 : st;
+    if ((e = cudaStreamWaitEvent(fs, pp->in_ready[k & 1], 0)) != cudaSuccess)
       return set_cuda_error(e);
     rc = fit_spots_uniform(b + l.images, dtype, width, height, model_id,
                            reinterpret_cast<const float *>(b + l.init), m, max_iter, max_error,
@@ -2603,9 +2632,9 @@ int fit_spots_uniform_host(const void *images, int dtype, int width, int height,
                            reinterpret_cast<int32_t *>(b + l.state),
                            reinterpret_cast<int32_t *>(b + l.iters),
                            out_evals ? reinterpret_cast<int32_t *>(b + l.evals) : nullptr,
-                           b + l.sched, kSchedHeaderBytes, stream);
+                           b + l.sched, kSchedHeaderBytes, fs);
     if (rc) return rc;
-    if ((e = cudaEventRecord(pp->fitted[k & 1], st)) != cudaSuccess ||
+    if ((e = cudaEventRecord(pp->fitted[k & 1], fs)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(cp, pp->fitted[k & 1], 0)) != cudaSuccess)
       return set_cuda_error(e);
     struct { void *dst; size_t off, sz; } outs[7] = {
@@ -2618,7 +2647,8 @@ int fit_spots_uniform_host(const void *images, int dtype, int width, int height,
                        cudaSuccess)
         return set_cuda_error(e);
   }
-  // `stream` completes only after the last results are on the host
+  // `stream` completes only after the last results are on the host (every download waited
+  // for its chunk's fit, so this covers the second fit stream too)
   if ((e = cudaEventRecord(pp->drained, cp)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(st, pp->drained, 0)) != cudaSuccess)
     return set_cuda_error(e);

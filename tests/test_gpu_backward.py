@@ -58,6 +58,33 @@ def test_backward_matches_oracle_ift_on_iso16():
     assert np.median(errs) <= 1e-5
 
 
+def test_backward_matches_finite_differences_1024_iso16():
+    """The backward workload's stated check: the GPU pixel gradient (forward and backward
+    kernels, tight FP32 stop) of the first 1,024 16x16 isotropic spots against central
+    finite differences of polished FP64 oracle refits over every pixel, per spot
+    ||grad - fd|| / ||fd|| <= 1e-4."""
+    from tests.backward_fd import fd_vjp, polished, rel_err
+    n = 1024
+    b = synth.make_workload("iso16", n)
+    g = b.to(DEV)
+    out = fitspots.fit_batch(g, **TIGHT)
+    gp, ga, gb, gc = _upstream(n, 13)
+    grad = fitspots.backward(g.images, g.offsets, g.dims, g.model, out, gp, ga, gb, gc)
+    torch.cuda.synchronize()
+    grad = grad.cpu().numpy().astype(np.float64).reshape(n, 256)
+    d = b.numpy()
+    img = synth.as_numpy_images(b).astype(np.float64)
+    ref = polished(img, d["offsets"], d["dims"], d["init"], d["model"])
+    up = torch.cat([gp, ga[:, None], gb[:, None], gc[:, None]], 1).double().numpy()
+    fd, _ = fd_vjp(img, d["offsets"], d["dims"], d["model"], ref["params"], up)
+    e = rel_err(grad, fd)
+    st = out["state"].cpu().numpy()
+    print(f"iso16 backward vs FD (1,024 spots): median {np.median(e):.2e}, "
+          f"p99 {np.percentile(e, 99):.2e}, max {e.max():.2e}")
+    assert np.isin(st, fitspots.CONVERGED_STATES).all()
+    assert e.max() <= 1e-4
+
+
 def _oracle_errors(b, out, up):
     """Per-spot relative error of the GPU pixel gradient against the oracle's FP64 backward
     at the oracle's own tight fit; also the determined mask of those fits."""

@@ -2,12 +2,15 @@
 
 The bar (per spot): centre within 1e-3 px, sigma, alpha and beta within 1e-4 relative,
 and the same convergence class (converged = MIN_DELTA, MIN_STEP, MAX_ERROR, NO_DECREASE).
-It is asserted on determined spots: the FP64 fit converged to a positive amplitude above
-the noise, no parameter is held at the limit() box, and its own normal matrix gives a
-centre standard error <= 0.1 px and a width standard error <= 10 %. All-spot agreement is
-asserted at a looser level because on a flat chi^2 surface (dim spots, widths running to
-the box) the min_delta stop leaves end points that move with rounding in any two
-implementations.
+On determined spots (the FP64 fit converged to a positive amplitude above the noise, no
+parameter held at the limit() box, centre standard error <= 0.1 px, width standard error
+<= 10 %) both are asserted at 0.999. On all spots, class agreement is asserted at 0.999
+(0.998 for the mixed sizes) and the share of converged fits inside the bar at 0.98: on flat
+chi^2 surfaces (widths near the ROI size, dim or negative amplitudes) FP32 model values
+alone move the min_delta stop point beyond the bar, even with everything after them in
+FP64 (the oracle's FP32-profile build keeps only 0.9974 of ell32 and 0.9958 of mixed
+converged fits inside it, tests/test_oracle_fp32_floor.py); the kernels' FP32 sums and
+separable assembly add to that on the same spots (measured 0.985-0.987).
 """
 import numpy as np
 import pytest
@@ -35,16 +38,17 @@ def _fit(batch, **kw):
 
 
 def _report(name, m):
-    print(f"{name}: n={m['n']} class {m['class_agree']:.5f} bar(conv) {m['bar_converged']:.5f} "
+    print(f"{name}: n={m['n']} class {m['class_agree']:.5f} state {m['state_agree']:.5f} "
+          f"bar(conv) {m['bar_converged']:.5f} "
           f"determined {m['n_well_posed']} class {m['class_agree_wp']:.5f} bar {m['bar_wp']:.5f} "
           f"max|dxy| {m['max_dxy_wp']:.2e}")
 
 
 @pytest.mark.parametrize("name,n,all_class,all_bar", [
-    ("iso15", 10_000, 0.999, 0.995),
-    ("iso16", 20_000, 0.999, 0.995),
-    ("ell32", 20_000, 0.995, 0.97),
-    ("mixed", 20_000, 0.995, 0.97),
+    ("iso15", 10_000, 0.999, 0.999),
+    ("iso16", 20_000, 0.999, 0.999),
+    ("ell32", 20_000, 0.999, 0.98),
+    ("mixed", 20_000, 0.998, 0.98),
 ])
 def test_parity_against_oracle(name, n, all_class, all_bar):
     b = synth.make_workload(name, n)
@@ -73,7 +77,7 @@ def test_full_size_ell32_sampled():
     m = compare(o, ref, sub.dims.numpy(), determined(sub, ref))
     _report("ell32-full-sample", m)
     assert m["class_agree_wp"] >= 0.999 and m["bar_wp"] >= 0.999
-    assert m["class_agree"] >= 0.995
+    assert m["class_agree"] >= 0.998 and m["bar_converged"] >= 0.98
     conv = np.isin(out["state"].cpu().numpy(), (1, 2, 3, 4))
     assert conv.mean() > 0.9
 
@@ -95,7 +99,7 @@ def test_full_size_mixed_sampled():
     _report("mixed-full-sample", m)
     assert m["n_well_posed"] >= 0.25 * idx.size
     assert m["class_agree_wp"] >= 0.999 and m["bar_wp"] >= 0.999
-    assert m["class_agree"] >= 0.995 and m["bar_converged"] >= 0.97
+    assert m["class_agree"] >= 0.998 and m["bar_converged"] >= 0.98
     st = out["state"].cpu().numpy()
     assert np.isin(st, (1, 2, 3, 4)).mean() > 0.9 and not np.isin(st, (-2,)).any()
 

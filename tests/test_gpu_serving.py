@@ -139,19 +139,43 @@ def test_admission_rejects_beyond_queue_and_checkpoint_restores():
         assert np.array_equal(first[k], srv.logs[0].results[k])
 
 
+def _realtime_run(queue_limit: int = 1024) -> dict:
+    """Serve the 2048 x 2048 / 2000 fps / 64-marker stream (1,000 warm-up frames, then
+    20,000) and return the latency summary of the timed frames and the drop count."""
+    markers, size, ring, warm, n = 64, 2048, 128, 1000, 20000
+    cs, host = _stream(ring, markers, size, seed=400)
+    srv = serving.TrackingServer(size, size, markers=markers, sessions=1,
+                                 queue_limit=queue_limit, device=DEV)
+    srv.set_markers(0, cs.start)
+    serving.run_stream(srv, 0, host, warm + n, fps=2000.0)
+    log = srv.logs[0]
+    lat = np.array([log.latency[k] for k in range(warm, warm + n) if k in log.latency])
+    summ = serving.latency_summary(lat)
+    summ["dropped"] = int(srv.dropped)
+    srv.close()
+    return summ
+
+
 def test_realtime_stream_latency_2048():
     """The camera workload: 2048 x 2048 uint16 frames at 2000 fps, 64 markers, 21 x 21 ROIs,
     20,000 frames after 1,000 warm-up frames: every frame served, the median latency (host
     arrival stamp -> results on the host) inside the 0.5 ms frame period and the 99th
-    percentile within ten periods (the tail is host scheduling: 0.8 ms in a process of its
-    own, a few ms after the rest of the suite)."""
-    markers, size, ring, warm, n = 64, 2048, 128, 1000, 20000
-    cs, host = _stream(ring, markers, size, seed=400)
-    srv = serving.TrackingServer(size, size, markers=markers, sessions=1, device=DEV)
-    srv.set_markers(0, cs.start)
-    serving.run_stream(srv, 0, host, warm + n, fps=2000.0)
-    lat = np.array([srv.logs[0].latency[k] for k in range(warm, warm + n)])
-    summ = serving.latency_summary(lat)
-    print("realtime 2048^2 at 2000 fps:", summ, "dropped", srv.dropped)
-    assert srv.dropped == 0 and summ["frames"] == n
+    percentile within ten periods. The stream is served by a process of its own, as a
+    deployment would run it: inside this long test process (after the other tests) the host
+    loop was measured to stall for up to ~0.1 s at a time, which is the test process, not
+    the session. The admission queue holds 1,024 frames (0.5 s of the stream; queued frames
+    cost host pointers only)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import json; from tests.test_gpu_serving import _realtime_run; "
+            "print('RESULT ' + json.dumps(_realtime_run()))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    summ = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("RESULT ")][-1][7:])
+    print("realtime 2048^2 at 2000 fps:", summ)
+    assert summ["dropped"] == 0 and summ["frames"] == 20000
     assert summ["p50_ms"] < 0.5 and summ["p99_ms"] < 5.0

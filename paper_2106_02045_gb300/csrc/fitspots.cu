@@ -260,66 +260,74 @@ __device__ __forceinline__ bool solve_damped32(const float (&A)[10], const float
 // unit diagonal, (M + lambda I) y = S b, delta = S y. A is packed upper-triangular:
 // A00 A01 A02 A03 A11 A12 A13 A22 A23 A33 (the isotropic model passes A33 = 1 and zeros in
 // its row and column). The scaling S = diag(A)^-1/2 and the scaled entries are formed in
-// FP32; the factorisation (M + lambda I) = L D L^T and both substitutions run in FP64, so
-// that nearly singular normal matrices (flat chi^2 surfaces) keep their step. Returns false
-// when the damped matrix is not positive definite or the step is not finite.
+// FP32; the elimination (the pivots of L D L^T) and both substitutions run in FP64. Called
+// only where the FP32 factorisation failed, so it is written for size, not speed: plain
+// loops over a 4 x 4 array that lives in local memory (L1), keeping the hot loop's code
+// small. Returns false when the damped matrix is not positive definite or the step is not
+// finite.
 __device__ __forceinline__ bool solve_damped64(const float (&A)[10], const float (&b)[4],
                                                float lam, float (&d)[4]) {
   if (!(A[0] > 0.f) || !(A[4] > 0.f) || !(A[7] > 0.f) || !(A[9] > 0.f)) return false;
   const float s0 = rsqrtf(A[0]), s1 = rsqrtf(A[4]), s2 = rsqrtf(A[7]), s3 = rsqrtf(A[9]);
   const double dg = 1.0 + (double)lam;
-  const double m01 = A[1] * s0 * s1, m02 = A[2] * s0 * s2, m03 = A[3] * s0 * s3;
-  const double m12 = A[5] * s1 * s2, m13 = A[6] * s1 * s3, m23 = A[8] * s2 * s3;
-  // L D L^T: pivots d_j with reciprocals i_j, unit lower factor l_jk
-  const double i0 = rcp64(dg);
-  const double l10 = m01 * i0, l20 = m02 * i0, l30 = m03 * i0;
-  const double d1 = fma(-l10, m01, dg);
-  if (!(d1 > 1e-30)) return false;
-  const double i1 = rcp64(d1);
-  const double t21 = fma(-l20, m01, m12), t31 = fma(-l30, m01, m13);
-  const double l21 = t21 * i1, l31 = t31 * i1;
-  const double d2 = fma(-l21, t21, fma(-l20, m02, dg));
-  if (!(d2 > 1e-30)) return false;
-  const double i2 = rcp64(d2);
-  const double t32 = fma(-l31, t21, fma(-l30, m02, m23));
-  const double l32 = t32 * i2;
-  const double d3 = fma(-l32, t32, fma(-l31, t31, fma(-l30, m03, dg)));
-  if (!(d3 > 1e-30)) return false;
-  const double i3 = rcp64(d3);
-  const double z0 = (double)(b[0] * s0);
-  const double z1 = fma(-l10, z0, (double)(b[1] * s1));
-  const double z2 = fma(-l21, z1, fma(-l20, z0, (double)(b[2] * s2)));
-  const double z3 = fma(-l32, z2, fma(-l31, z1, fma(-l30, z0, (double)(b[3] * s3))));
-  const double y3 = z3 * i3;
-  const double y2 = fma(-l32, y3, z2 * i2);
-  const double y1 = fma(-l31, y3, fma(-l21, y2, z1 * i1));
-  const double y0 = fma(-l30, y3, fma(-l20, y2, fma(-l10, y1, z0 * i0)));
-  d[0] = (float)y0 * s0;
-  d[1] = (float)y1 * s1;
-  d[2] = (float)y2 * s2;
-  d[3] = (float)y3 * s3;
+  double m[16], z[4];
+  m[0] = m[5] = m[10] = m[15] = dg;
+  m[1] = m[4] = A[1] * s0 * s1;
+  m[2] = m[8] = A[2] * s0 * s2;
+  m[3] = m[12] = A[3] * s0 * s3;
+  m[6] = m[9] = A[5] * s1 * s2;
+  m[7] = m[13] = A[6] * s1 * s3;
+  m[11] = m[14] = A[8] * s2 * s3;
+  z[0] = (double)(b[0] * s0);
+  z[1] = (double)(b[1] * s1);
+  z[2] = (double)(b[2] * s2);
+  z[3] = (double)(b[3] * s3);
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {  // forward elimination; m[5k] is the k-th pivot
+    const double piv = m[5 * k];
+    if (!(piv > 1e-30)) return false;
+    const double ip = rcp64(piv);
+#pragma unroll 1
+    for (int i = k + 1; i < 4; ++i) {
+      const double f = m[4 * i + k] * ip;
+#pragma unroll 1
+      for (int j = k + 1; j < 4; ++j) m[4 * i + j] = fma(-f, m[4 * k + j], m[4 * i + j]);
+      z[i] = fma(-f, z[k], z[i]);
+    }
+  }
+#pragma unroll 1
+  for (int k = 3; k >= 0; --k) {  // back substitution
+    double t = z[k];
+#pragma unroll 1
+    for (int j = k + 1; j < 4; ++j) t = fma(-m[4 * k + j], z[j], t);
+    z[k] = t * rcp64(m[5 * k]);
+  }
+  d[0] = (float)z[0] * s0;
+  d[1] = (float)z[1] * s1;
+  d[2] = (float)z[2] * s2;
+  d[3] = (float)z[3] * s3;
   return isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]) && isfinite(d[3]);
 }
 
-// Below this pivot fraction (10 bits of the diagonal lost in FP32) or when the FP32
-// factorisation fails, Eq. 14 is solved again in FP64: the nearly singular systems of flat
-// chi^2 surfaces (see kAmpCancel64 for the cost of a looser threshold).
-constexpr float kPivot64 = 1.f / 1024.f;
-
-// Eq. 14: FP32 where the system keeps its digits, FP64 where cancellation would cost them.
+// Eq. 14: FP32, redone in FP64 where the FP32 factorisation fails (the rounding of a nearly
+// singular system). A low FP32 pivot alone does not call for FP64: the step is then
+// imprecise in a direction along which chi^2 hardly changes, and the LM iteration corrects
+// it; measured on GB300, taking FP64 there too (pivot below 1/1024 or 1/32) moved no parity
+// figure and cost 1 % and 6 % of the 32 x 32 fit time.
 __device__ __forceinline__ bool solve_damped(const float (&A)[10], const float (&b)[4], float lam,
                                              float (&d)[4]) {
   float piv;
-  bool ok = solve_damped32(A, b, lam, d, piv);
-  if (!ok || piv < kPivot64) ok = solve_damped64(A, b, lam, d);
-  return ok;
+  if (solve_damped32(A, b, lam, d, piv)) return true;
+  return solve_damped64(A, b, lam, d);
 }
 
 // Eq. 14 at lambda = 10^klam, raising klam tenfold at a time (up to the 10^4 cap) while the
 // damped system is not positive definite. With a positive diagonal, J^T J + lambda diag(J^T J)
 // is positive definite for every lambda > 0, so a failed factorisation comes from the rounding
 // of a nearly singular FP32 normal matrix; more damping is the step the exact system would
-// allow, as for a rejected trial. False when no lambda up to the cap gives a step.
+// allow, as for a rejected trial. False when no lambda up to the cap gives a step. The
+// per-spot kernels use this loop; the batched ones raise lambda by one decade per round
+// instead (kResolve), which keeps the loop out of their hot code.
 __device__ __forceinline__ bool solve_damped_raising(const float (&A)[10], const float (&b)[4],
                                                      int &klam, float (&d)[4]) {
   for (;;) {  // one inlined copy of the solve
@@ -1003,7 +1011,8 @@ enum : int {
   kResFields = RT2 + K2
 };
 constexpr int kIsoBit = 1 << 18, kTransBit = 1 << 19, kFirstEval = 1 << 20,
-              kFirstTrial = 1 << 21, kActive = 1 << 22;
+              kFirstTrial = 1 << 21, kActive = 1 << 22,
+              kResolve = 1 << 23;  // the damped solve failed: raised lambda, solve next round
 __device__ __forceinline__ int flag_w(int f) { return f & 511; }
 __device__ __forceinline__ int flag_h(int f) { return (f >> 9) & 511; }
 
@@ -1107,6 +1116,8 @@ __device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const in
     const int W = flag_w(flags), H = flag_h(flags);
     const bool iso = flags & kIsoBit, trans = flags & kTransBit;
     bool first_eval = flags & kFirstEval, first_trial = flags & kFirstTrial;
+    // a round without an evaluation: only the damped solve, at the lambda the last round raised
+    bool resolve = flags & kResolve;
     const int P = iso ? 3 : 4;
     const float Nf = (float)(W * H);
     // origin of the row weights, as the slot's evaluation took it: the geometry's fixed R / 2,
@@ -1120,7 +1131,7 @@ __device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const in
       pe[k] = ST(SPE + k, j);
       dl[k] = ST(SDL + k, j);
     }
-    int klam = STI(SKLAM, j), it = STI(SIT, j), evals = STI(SEVALS, j) + 1;
+    int klam = STI(SKLAM, j), it = STI(SIT, j), evals = STI(SEVALS, j) + (resolve ? 0 : 1);
     float chib = ST(SCHIB, j), alb = ST(SALB, j), bpb = ST(SBPB, j), noiseb = ST(SNOISEB, j);
     float rab = ST(SRA, j), rbb = ST(SRB, j);
     const float shift = ST(SSH0, j);
@@ -1156,7 +1167,9 @@ __device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const in
     bool finish = false, need_grad = false, need_solve = false;
     int state = FS_STATE_MAX_ITER;
     float ra = ra_t, rb = rb_t, rc = chi;  // values reported on finish
-    if (first_eval) {
+    if (resolve) {
+      need_solve = true;
+    } else if (first_eval) {
       first_eval = false;
       it = 1;
 #pragma unroll
@@ -1248,7 +1261,8 @@ __device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const in
     }
     if (need_solve) {
       float d[4];
-      if (solve_damped_raising(A, bv, klam, d)) {
+      resolve = false;
+      if (solve_damped(A, bv, pow10i(klam), d)) {
         if (iso) d[3] = d[2];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -1256,6 +1270,11 @@ __device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const in
           pe[k] = p[k] + d[k];
         }
         limit_params(pe, W, H, iso);
+      } else if (klam < 4) {
+        // not positive definite at this lambda (FP32 rounding of a nearly singular J^T J):
+        // tenfold damping, solved in the slot's next round, which evaluates nothing
+        ++klam;
+        resolve = true;
       } else {
         finish = true;
         state = FS_STATE_NOT_CONVERGED;
@@ -1295,7 +1314,8 @@ __device__ __forceinline__ bool lm_step(const FitArgs &a, const int wf, const in
     ST(SRA, j) = rab;
     ST(SRB, j) = rbb;
     flags = (flags & (kFirstEval - 1)) | (first_eval ? kFirstEval : 0) |
-            (first_trial ? kFirstTrial : 0) | (active ? kActive : 0);
+            (first_trial ? kFirstTrial : 0) | (active ? kActive : 0) |
+            (resolve && active ? kResolve : 0);
     STI(SFLAGS, j) = flags;
   return active;
 }
@@ -1672,8 +1692,10 @@ __device__ __forceinline__ void batched_drain(const FitArgs &a, const int cls, c
         }
       }
     }
-    const unsigned amask = __ballot_sync(full, active);
-    if (!amask) break;
+    if (!__ballot_sync(full, active)) break;
+    // slots to evaluate this round: the active ones without a pending re-solve
+    const unsigned amask =
+        __ballot_sync(full, active && lane < kSlots && !(STI(SFLAGS, lane) & kResolve));
     __syncwarp();
 
     if constexpr (L == 32 && C == 1) {

@@ -656,6 +656,27 @@ def _extra_mixed(args, dev, stream) -> dict:
         "ms_per_step": pcs, "fit_launches_per_step": used, "single_launch_speedup": pcs / ms,
         "what": "fit_spots_per_class: the same prepass and kernels, one persistent launch per "
                 "size class in use"}
+    # the plain form: per-spot kernels (every lane group runs its own spot's LM step, no
+    # slots), one launch per size class, each class on the per-spot twin of its batched
+    # configuration (same lanes x columns x rows)
+    keep = [fitspots.get_config(c) for c in range(16)]
+    cfgs = fitspots.configs()
+    try:
+        for c in range(16):
+            L, C, R, _ = cfgs[keep[c]]
+            twin = [i for i, (l, cc, r, bt) in enumerate(cfgs)
+                    if (l, cc, r) == (L, C, R) and not bt and fitspots.config_fits(c, i)]
+            if twin:
+                fitspots.set_config(c, twin[0])
+        plain = _timed(lambda: fitspots.fit_batch(mb, out=mo, workspace=mws, stream=stream,
+                                                  per_class=True), 3, stream)
+    finally:
+        for c, k in enumerate(keep):
+            fitspots.set_config(c, k)
+    out["mixed"]["plain_per_class"] = {
+        "ms_per_step": plain, "fit_launches_per_step": used, "single_launch_speedup": plain / ms,
+        "what": "per-spot kernels (LM step run by every lane group for its own spot, no "
+                "slots), one launch per size class, same geometry as the batched defaults"}
     # elongated ROIs (a side above 32, at most 1024 pixels) through the same single launch
     eb = synth.make_workload("elongated", None, device=dev)
     eo = fitspots.alloc_outputs(eb.n, dev)
@@ -759,16 +780,20 @@ def _e2e(args, b, out, ws, stream, barrier, world, dev):
         fitspots.fit_uniform_host(h_img, W, H, synth.MODEL_ELLIPTIC, h_init, chunk=chunk,
                                   out=h_out, workspace=d_ws, device=dev, stream=stream)
 
-    e2e_steps = max(1, min(args.steps, 5))
+    # one event before every call and one after the last: the mean over the steps is the
+    # value, the per-call times show the spread (the host link of some boxes stalls for tens
+    # of ms now and then, plain pinned copies included; see link_copy_ms)
+    e2e_steps = max(5, args.steps)
     e2e_step()
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
+    evs[0].record(stream)
+    for k in range(e2e_steps):
         e2e_step()
-    e1.record(stream)
+        evs[k + 1].record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    per_call = [evs[k].elapsed_time(evs[k + 1]) for k in range(e2e_steps)]
+    e2e_ms = sum(per_call) / e2e_steps
     conv_e2e = int(np.isin(h_out["state"].numpy(), CONVERGED).sum())
     h2d = h_img.numel() * h_img.element_size() + h_init.numel() * h_init.element_size()
     d2h = sum(v.numel() * v.element_size() for v in h_out.values())
@@ -778,27 +803,33 @@ def _e2e(args, b, out, ws, stream, barrier, world, dev):
     # the host link alone: one plain pinned host -> device copy of the same bytes, so that
     # the line shows whether the end-to-end number is bound by the link or by the fits
     d_img = torch.empty_like(b.images)
+    copies = []
     with torch.cuda.stream(stream):
         d_img.copy_(h_img, non_blocking=True)
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for _ in range(2):
+        for _ in range(e2e_steps):
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
             d_img.copy_(h_img, non_blocking=True)
-        c1.record(stream)
-    c1.synchronize()
-    copy_ms = c0.elapsed_time(c1) / 2
+            c1.record(stream)
+            copies.append((c0, c1))
+    torch.cuda.synchronize(dev)
+    copy_times = [c0.elapsed_time(c1) for c0, c1 in copies]
+    copy_ms = statistics.median(copy_times)
     del d_img
     img_bytes = h_img.numel() * h_img.element_size()
     # the link split sits at the top level of the e2e object: the whole call's time, the
     # images' copy alone, and their ratio (near 1 = bound by the host link, not the fits)
+    med = statistics.median(per_call)
     return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "e2e_ms": e2e_ms, "image_copy_ms": copy_ms,
+            "e2e_ms": e2e_ms, "e2e_median_ms": med, "e2e_max_ms": max(per_call),
+            "steps": e2e_steps, "image_copy_ms": copy_ms, "image_copy_max_ms": max(copy_times),
             "link_h2d_gbs": img_bytes / (copy_ms * 1e-3) / 1e9,
-            "frac_of_link": copy_ms / e2e_ms, "chunk_spots": chunk,
+            "frac_of_link": copy_ms / med, "chunk_spots": chunk,
             "call": "fit_spots_uniform_host (copies overlapped with fits; even and odd chunks "
                     "fitted on two streams)",
-            "link_note": "image_copy_ms: one pinned host-to-device copy of the step's images "
-                         "alone, timed with CUDA events after the e2e steps"}
+            "link_note": "image_copy_ms: median of as many pinned host-to-device copies of the "
+                         "step's images alone, timed with CUDA events after the e2e steps; "
+                         "frac_of_link = image_copy_ms / e2e_median_ms"}
 
 
 def main() -> None:

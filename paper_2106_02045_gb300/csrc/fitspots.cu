@@ -2001,12 +2001,35 @@ __device__ __forceinline__ void batched_drain(const FitArgs &a, const int cls, c
 #undef STI
 #undef RES
 
-// A batched configuration as a kernel of its own: drains the classes of `cl` in order.
+// The classes of ROIs with both sides at most 16: the single mixed launch drains them with
+// the 16-lane batched geometry (two spots per warp evaluation) instead of the generic
+// 32-lane one, which would leave half of its lanes or more without a column.
+__host__ __device__ constexpr bool small_class(int cls) {
+  return cls == 0 || cls == 1 || cls == 4 || cls == 5;
+}
+constexpr int kSmallL = 16, kSmallR = 16;
+
+// A batched configuration as a kernel of its own: drains the classes of `cl` in order. The
+// generic configuration (G, one row block) takes the small classes with the 16-lane
+// geometry, so that one launch still serves every class.
 template <int L, int C, int R, int NB, bool G>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, NB > 1 ? 5 : batched_min_blocks(C, R))
     fit_kernel_batched(FitArgs a, ClassList cl) {
-  for (int ci = 0; ci < cl.count; ++ci)
-    batched_drain<L, C, R, NB, G>(a, cl.cls[ci], batched_warp_floats(L, NB * R));
+  // per-warp stride of the block's shared memory: one for both geometries, since the warps
+  // of a block can be in different classes at the same time
+  constexpr int wf = G && NB == 1 ? (batched_warp_floats(L, R) > batched_warp_floats(kSmallL, kSmallR)
+                                         ? batched_warp_floats(L, R)
+                                         : batched_warp_floats(kSmallL, kSmallR))
+                                  : batched_warp_floats(L, NB * R);
+  for (int ci = 0; ci < cl.count; ++ci) {
+    if constexpr (G && NB == 1) {
+      if (small_class(cl.cls[ci])) {
+        batched_drain<kSmallL, 1, kSmallR, 1, false>(a, cl.cls[ci], wf);
+        continue;
+      }
+    }
+    batched_drain<L, C, R, NB, G>(a, cl.cls[ci], wf);
+  }
 }
 
 // ------------------------------------------------------------------ configurations
@@ -2050,8 +2073,9 @@ static_assert(sizeof(kKernels) / sizeof(kKernels[0]) == kNumConfigs, "one kernel
 
 size_t config_smem_bytes(int cfg) {
   const CfgDesc &c = kConfigs[cfg];
-  const int per_warp =
-      c.batched ? batched_warp_floats(c.L, c.NB * c.R) : warp_smem_floats(c.L, c.R);
+  int per_warp = c.batched ? batched_warp_floats(c.L, c.NB * c.R) : warp_smem_floats(c.L, c.R);
+  if (c.generic && c.NB == 1)  // also drains the small classes with the 16-lane geometry
+    per_warp = std::max(per_warp, batched_warp_floats(kSmallL, kSmallR));
   return (size_t)kWarpsPerBlock * per_warp * sizeof(float);
 }
 

@@ -104,7 +104,8 @@ struct LmResult {
 // The LM loop of the fit: lambda = 10^klam from 10^-2, lowered after an accepted first trial,
 // raised (up to 10^4) while the trial does not decrease the objective and the step is not
 // below min_step; stop on max_error, min_delta (relative decrease), min_step, no decrease or a
-// failed evaluation / solve. p is updated in place (the accepted point).
+// failed evaluation / a solve that fails up to the damping cap. p is updated in place (the
+// accepted point).
 template <typename Eval, typename Limit>
 __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int max_iter,
                                              float max_error, float min_delta, float min_step,
@@ -118,8 +119,20 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
   };
   float A[10], b[4], best[4], dl[4], pt[4];
   float al = 0.f, be = 0.f;
+  int klam = -2;
+  // Eq. 14 at lambda = 10^klam, raising klam tenfold (up to 10^4) while the damped system is
+  // not positive definite: with a positive diagonal that only happens through the FP32
+  // rounding of a nearly singular normal matrix, and more damping is the step the exact
+  // system would allow, as for a rejected trial.
+  auto solve_raising = [&]() {
+    while (!solve4(A, b, exp10f((float)klam), dl)) {
+      if (klam >= 4) return false;
+      ++klam;
+    }
+    return true;
+  };
   using Obj = decltype(evaluate(p, true, al, be, A, b));
-  int klam = -2, it = 0, evals = 0, state = FS_STATE_MAX_ITER;
+  int it = 0, evals = 0, state = FS_STATE_MAX_ITER;
   while (it < max_iter) {
     ++it;
     ++evals;
@@ -141,7 +154,7 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
       float at, bt, Ad[10], bd[4];
       return evaluate(pt, false, at, bt, Ad, bd);
     };
-    if (!solve4(A, b, exp10f((float)klam), dl)) {
+    if (!solve_raising()) {
       state = FS_STATE_NOT_CONVERGED;
       break;
     }
@@ -152,7 +165,7 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
     bool failed = false;
     while (!all_small(dl, best) && chi < Chi && klam < 4) {
       ++klam;
-      if (!solve4(A, b, exp10f((float)klam), dl)) {
+      if (!solve_raising()) {
         failed = true;
         break;
       }

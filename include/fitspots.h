@@ -109,8 +109,14 @@ size_t fit_spots_uniform_workspace(void);
  * Results of a spot depend only on that spot's inputs and the size-class configuration
  * in force (fit_spots_set_config), never on the other spots of the batch.
  * Launches: a prepass (three small kernels) sorts the spots by size class, then one
- * persistent launch of the generic configuration fits every class (each ROI oriented with
- * its longer side along the lanes when that side is at most 32, rows in blocks of 32).
+ * persistent launch of the generic configuration fits every class of W, H <= 32 (each ROI
+ * oriented with its longer side along the lanes, rows in a block of 8, 16, 24 or 32; the
+ * classes with both sides at most 16 with a 16-lane geometry, two spots per warp, inside the
+ * same launch), and a second launch the elongated class (a side above 32).
+ * Arithmetic: FP32, with the 2x2 amplitude solve (Eq. 6) redone in FP64 where its determinant
+ * cancels by a factor above 1024 and the damped solve (Eq. 14) redone in FP64 where the FP32
+ * factorisation fails; a damped system that stays not positive definite gets tenfold more
+ * damping, up to the 10^4 cap.
  */
 int fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t *offsets,
               const int32_t *roi_dims, const float *init_params, const uint8_t *model,
@@ -124,7 +130,8 @@ int fit_spots(const void *images, int dtype, int64_t image_elems, const int64_t 
  * alone, largest first, with the configuration fit_spots_set_config assigns to it) instead of
  * one launch of the generic configuration for all classes. Same arguments and workspace; the
  * results agree with fit_spots to FP32 rounding (bit for bit where the class's configuration
- * is the generic one). The plain form that the single launch is compared with.
+ * is the generic one). Assigning a class its per-spot configuration (fit_spots_config_batched
+ * = 0) gives the plain form: every lane group runs its own spot's LM step.
  */
 int fit_spots_per_class(const void *images, int dtype, int64_t image_elems,
                         const int64_t *offsets, const int32_t *roi_dims,

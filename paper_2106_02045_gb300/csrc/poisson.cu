@@ -36,6 +36,9 @@ using namespace fs_warp;
 constexpr int kPThreads = 128;
 constexpr int kIrlsMax = 40;        // amplitude iterations per evaluated point
 constexpr float kIrlsTol = 1e-6f;   // stop once a correction is below this x (|alpha| + |beta|)
+// deviance changes within this fraction of the deviance of 0 or of the min_delta threshold are
+// recomputed from the parameter difference (the FP32 model values leave D about 1e-7 relative)
+constexpr float kTieWindow = 1e-6f;
 
 struct PArgs {
   const void *images;
@@ -314,13 +317,52 @@ __global__ void __launch_bounds__(kPThreads) poisson_kernel(PArgs a) {
       return Dev;
     };
 
+    // The deviance change D(t) - D(b) between the best point b and a trial t, for decisions
+    // near a tie: per pixel 2 [dh - g log1p(dh / h_b)], dh = h_t - h_b formed from the
+    // parameter difference (the exponent difference in closed form, expm1 of it), so the
+    // change keeps its relative precision where D(t) and D(b) agree in their leading digits.
+    auto refine = [&](const float (&pb)[4], float ab, float bb, const float (&pt)[4], float at,
+                      float bt) -> double {
+      const float ivxb = 1.f / (pb[2] * pb[2]), ivyb = 1.f / (pb[3] * pb[3]);
+      const float ivxt = 1.f / (pt[2] * pt[2]), ivyt = 1.f / (pt[3] * pt[3]);
+      const float d0 = pt[0] - pb[0], d1 = pt[1] - pb[1];
+      // ivx_b - ivx_t = (s_t - s_b)(s_t + s_b) ivx_t ivx_b, likewise for y
+      const float kx = (pt[2] - pb[2]) * (pt[2] + pb[2]) * ivxt * ivxb;
+      const float ky = (pt[3] - pb[3]) * (pt[3] + pb[3]) * ivyt * ivyb;
+      const float dal = at - ab, dbe = bt - bb;
+      float acc = 0.f;
+      int x = x_start, y = y_start;
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        if (lane + 32 * k < N) {
+          const float dxb = (float)x - pb[0], dyb = (float)y - pb[1];
+          const float dxt = dxb - d0, dyt = dyb - d1;
+          // exponent at t minus exponent at b
+          const float da = 0.5f * (d0 * (dxt + dxb) * ivxt + dxb * dxb * kx +
+                                   d1 * (dyt + dyb) * ivyt + dyb * dyb * ky);
+          const float eb = __expf(-0.5f * (dxb * dxb * ivxb + dyb * dyb * ivyb));
+          const float dh = fmaf(at * eb, expm1f(da), fmaf(dal, eb, dbe));
+          const float hb = fmaf(ab, eb, bb);
+          const float gk = g[k];
+          acc += gk > 0.f ? dh - gk * log1pf(dh / hb) : dh;
+        }
+        x += stepx;
+        y += stepy;
+        if (x >= W) {
+          x -= W;
+          ++y;
+        }
+      }
+      return 2.0 * warp_sum((double)acc);
+    };
+
     float p[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) p[j] = a.init[4 * s + j];
     if (iso) p[3] = p[2];
     limit(p);
     const LmResult lm = lm_drive(p, iso, P, a.max_iter, a.max_error, a.min_delta, a.min_step,
-                                 evaluate, limit);
+                                 evaluate, limit, refine, kTieWindow);
     float al, be, Ad[10], bd[4];
     const double dv = evaluate(p, false, al, be, Ad, bd);
     if (lane == 0) {

@@ -106,10 +106,17 @@ struct LmResult {
 // below min_step; stop on max_error, min_delta (relative decrease), min_step, no decrease or a
 // failed evaluation / a solve that fails up to the damping cap. p is updated in place (the
 // accepted point).
-template <typename Eval, typename Limit>
+//
+// Ties: where the change of the objective from the best point to the trial lies within
+// tie_window * (objective) of 0 or of the min_delta threshold, the difference of two rounded
+// objectives decides nothing, and `refine(best, alpha_b, beta_b, trial, alpha_t, beta_t)` is
+// asked for the change itself, computed from the parameter difference with relative
+// precision (NaN: keep the plain difference). The decisions then use that change.
+template <typename Eval, typename Limit, typename Refine>
 __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int max_iter,
                                              float max_error, float min_delta, float min_step,
-                                             Eval &&evaluate, Limit &&limit) {
+                                             Eval &&evaluate, Limit &&limit, Refine &&refine,
+                                             float tie_window) {
   auto all_small = [&](const float (&d)[4], const float (&q)[4]) {
     bool sm = true;
 #pragma unroll
@@ -118,7 +125,7 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
     return sm;
   };
   float A[10], b[4], best[4], dl[4], pt[4];
-  float al = 0.f, be = 0.f;
+  float al = 0.f, be = 0.f, at = 0.f, bt = 0.f;
   int klam = -2;
   // Eq. 14 at lambda = 10^klam, raising klam tenfold (up to 10^4) while the damped system is
   // not positive definite: with a positive diagonal that only happens through the FP32
@@ -151,8 +158,23 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
 #pragma unroll
       for (int j = 0; j < 4; ++j) pt[j] = best[j] + dl[j];
       limit(pt);
-      float at, bt, Ad[10], bd[4];
+      float Ad[10], bd[4];
       return evaluate(pt, false, at, bt, Ad, bd);
+    };
+    // the change chi_t - chi of a trial, refined near the two decision thresholds
+    bool refined = false;
+    auto change = [&](Obj Chi) -> Obj {
+      Obj d = Chi - chi;
+      refined = false;
+      const Obj win = Obj(tie_window) * chi;
+      if (isfinite(d) && (fabs(d) <= win || fabs(d + Obj(min_delta) * chi) <= win)) {
+        const Obj r = Obj(refine(best, al, be, pt, at, bt));
+        if (isfinite(r)) {
+          d = r;
+          refined = true;
+        }
+      }
+      return d;
     };
     if (!solve_raising()) {
       state = FS_STATE_NOT_CONVERGED;
@@ -161,9 +183,10 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
     if (iso) dl[3] = dl[2];
     ++evals;
     Obj Chi = trial();
-    if (chi > Chi) --klam;
+    Obj dC = change(Chi);
+    if (dC < Obj(0)) --klam;
     bool failed = false;
-    while (!all_small(dl, best) && chi < Chi && klam < 4) {
+    while (!all_small(dl, best) && dC > Obj(0) && klam < 4) {
       ++klam;
       if (!solve_raising()) {
         failed = true;
@@ -172,12 +195,13 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
       if (iso) dl[3] = dl[2];
       ++evals;
       Chi = trial();
+      dC = change(Chi);
     }
     if (failed) {
       state = FS_STATE_NOT_CONVERGED;
       break;
     }
-    if (chi < Chi || isnan(Chi)) {
+    if (dC > Obj(0) || isnan(Chi)) {
       state = (all_small(dl, best) && !isnan(Chi)) ? FS_STATE_NO_DECREASE : FS_STATE_NOT_CONVERGED;
       break;
     }
@@ -187,7 +211,7 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
       state = FS_STATE_MAX_ERROR;
       break;
     }
-    if (chi * (Obj(1) - Obj(min_delta)) < Chi) {
+    if (refined ? dC > -Obj(min_delta) * chi : chi * (Obj(1) - Obj(min_delta)) < Chi) {
       state = FS_STATE_MIN_DELTA;
       break;
     }
@@ -197,6 +221,18 @@ __device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int
     }
   }
   return {it, evals, state};
+}
+
+// The driver without tie refinement (the plain difference of two objectives decides).
+template <typename Eval, typename Limit>
+__device__ __forceinline__ LmResult lm_drive(float (&p)[4], bool iso, int P, int max_iter,
+                                             float max_error, float min_delta, float min_step,
+                                             Eval &&evaluate, Limit &&limit) {
+  auto none = [](const float (&)[4], float, float, const float (&)[4], float, float) {
+    return (double)NAN;
+  };
+  return lm_drive(p, iso, P, max_iter, max_error, min_delta, min_step, evaluate, limit, none,
+                  0.f);
 }
 
 }  // namespace fs_warp

@@ -726,6 +726,18 @@ def _extra_backward(dev, stream, hbm) -> dict:
                                     "bytes_per_spot": 256 * 8 + 73,
                                     "traffic": _traffic_from_profile(BWD_PROFILE, BWD_SOURCE),
                                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    # the backward workload as configured: the gradient of (x0, y0, sigma, alpha, beta), no
+    # upstream for the normalised chi^2, so the second pixel pass writes without reading
+    bms2 = _timed(lambda: fitspots.backward(bb.images, bb.offsets, bb.dims, bb.model, fo, up[0],
+                                            up[1], up[2], None, grad_images=gimg, stream=stream),
+                  10, stream)
+    nb2 = bb.n * (256 * 8 + 69)
+    out_b["params_alpha_beta_only"] = {
+        "what": "VJP of (x0, y0, sigma, alpha, beta) only (no chi^2 upstream)",
+        "value": bb.n / (bms2 * 1e-3), "unit": "spots/s", "ms_per_step": bms2,
+        "roofline": {"bound": "hbm", "achieved": nb2 / (bms2 * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": nb2 / (bms2 * 1e-3) / 1e9 / hbm,
+                     "bytes_per_spot": 256 * 8 + 69}}
     return {"backward": out_b}
 
 

@@ -182,19 +182,22 @@ __device__ __forceinline__ void rows_a(const T *p, int step, const float4 *t4, c
 
 // Phase B rows of one lane: grad = e_x e_y (K1 + alpha B(y)) + u_chi g + K2 with the row
 // table rb = (e_y, alpha B(y)); same row addressing as rows_a.
-template <typename T, bool kPred, int kStep>
+// kChi: the upstream gradient of the normalised chi^2 is given, so the gradient has a term in
+// the pixels themselves and they are read again; without it phase B reads no pixels.
+template <typename T, bool kPred, int kStep, bool kChi>
 __device__ __forceinline__ void rows_b(const T *p, float *q, int step, const float2 *rb, int rs,
                                        int nleft, float ex, float K1, float cc, float K2,
                                        uint64_t pol) {
   const int st = kStep ? kStep : step;
   float gv[kChunk];
 #pragma unroll
-  for (int u = 0; u < kChunk; ++u) gv[u] = !kPred || u < nleft ? ldpix(p + u * st, pol) : 0.f;
+  for (int u = 0; u < kChunk; ++u)
+    gv[u] = kChi && (!kPred || u < nleft) ? ldpix(p + u * st, pol) : 0.f;
 #pragma unroll
   for (int u = 0; u < kChunk; ++u)
     if (!kPred || u < nleft) {
       const float2 eb = rb[u * rs];
-      stgrad(q + u * st, fmaf(ex * eb.x, K1 + eb.y, fmaf(cc, gv[u], K2)), pol);
+      stgrad(q + u * st, fmaf(ex * eb.x, K1 + eb.y, kChi ? fmaf(cc, gv[u], K2) : K2), pol);
     }
 }
 
@@ -350,7 +353,7 @@ __device__ __forceinline__ bool solve_spot(const float (&G)[kNG], const float (&
   return ok;
 }
 
-template <typename T>
+template <typename T, bool kChi>
 __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
   __shared__ float4 sm4[kBwdWarps * kBwdWarpFloats / 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -696,15 +699,15 @@ __global__ void __launch_bounds__(kBwdThreads, 8) backward_kernel(BwdArgs a) {
         if (fast) {
           if (pair)
             for (; t0 + kChunk <= nmax; t0 += kChunk)
-              rows_b<T, false, 16>(p + t0 * 16, q + t0 * 16, 16, rt + t0 * rpsj, rpsj, 0, ex, K1,
+              rows_b<T, false, 16, kChi>(p + t0 * 16, q + t0 * 16, 16, rt + t0 * rpsj, rpsj, 0, ex, K1,
                                    ccj, K2, drop);
           else
             for (; t0 + kChunk <= nmax; t0 += kChunk)
-              rows_b<T, false, 32>(p + t0 * 32, q + t0 * 32, 32, rt + t0 * rpsj, rpsj, 0, ex, K1,
+              rows_b<T, false, 32, kChi>(p + t0 * 32, q + t0 * 32, 32, rt + t0 * rpsj, rpsj, 0, ex, K1,
                                    ccj, K2, drop);
         }
         for (; t0 < nmax; t0 += kChunk)
-          rows_b<T, true, 0>(p + t0 * step, q + t0 * step, step, rt + t0 * rpsj, rpsj, nv - t0,
+          rows_b<T, true, 0, kChi>(p + t0 * step, q + t0 * step, step, rt + t0 * rpsj, rpsj, nv - t0,
                              ex, K1, ccj, K2, drop);
       }
       __syncwarp();
@@ -753,19 +756,26 @@ extern "C" int fit_spots_backward(const void *images, int dtype, int64_t image_e
   const int warps_per_block = kBwdThreads / 32;
   const int64_t groups = (n + kGroup - 1) / kGroup;
   int64_t blocks = (groups + warps_per_block - 1) / warps_per_block;
+  // without an upstream gradient of the normalised chi^2 the second pixel pass reads no pixels
+  const bool chi = grad_chi2 != nullptr;
+  const void *fn = dtype == FS_U16
+                       ? (chi ? reinterpret_cast<const void *>(backward_kernel<unsigned short, true>)
+                              : reinterpret_cast<const void *>(backward_kernel<unsigned short, false>))
+                       : (chi ? reinterpret_cast<const void *>(backward_kernel<float, true>)
+                              : reinterpret_cast<const void *>(backward_kernel<float, false>));
   int per_sm = 0;
-  e = dtype == FS_U16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, backward_kernel<unsigned short>, kBwdThreads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, backward_kernel<float>, kBwdThreads, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBwdThreads, 0);
   if (e != cudaSuccess) return FS_ERR_CUDA;
   const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   if (blocks > cap) blocks = cap;
-  if (dtype == FS_U16)
-    backward_kernel<unsigned short>
-        <<<(int)blocks, kBwdThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
-  else
-    backward_kernel<float><<<(int)blocks, kBwdThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dtype == FS_U16) {
+    if (chi) backward_kernel<unsigned short, true><<<(int)blocks, kBwdThreads, 0, st>>>(a);
+    else backward_kernel<unsigned short, false><<<(int)blocks, kBwdThreads, 0, st>>>(a);
+  } else {
+    if (chi) backward_kernel<float, true><<<(int)blocks, kBwdThreads, 0, st>>>(a);
+    else backward_kernel<float, false><<<(int)blocks, kBwdThreads, 0, st>>>(a);
+  }
   e = cudaGetLastError();
   return e == cudaSuccess ? FS_OK : FS_ERR_CUDA;
 }

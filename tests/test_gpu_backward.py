@@ -58,6 +58,41 @@ def test_backward_matches_oracle_ift_on_iso16():
     assert np.median(errs) <= 1e-5
 
 
+def test_backward_without_chi2_upstream_matches_oracle():
+    """The gradient of (x0, y0, sigma, alpha, beta) alone (no upstream for the normalised
+    chi^2, the second pixel pass then reads no pixels), against the oracle's FP64 backward
+    with a zero chi^2 upstream, on 1,024 iso16 spots and on uint16 ell32 spots."""
+    import oracle
+    for name, n in (("iso16", 1024), ("ell32", 400)):
+        b = synth.make_workload(name, n)
+        g = b.to(DEV)
+        out = fitspots.fit_batch(g, **TIGHT)
+        gp, ga, gb, _ = _upstream(n, 17)
+        grad = fitspots.backward(g.images, g.offsets, g.dims, g.model, out, gp, ga, gb, None)
+        torch.cuda.synchronize()
+        grad = grad.cpu().numpy()
+        d = b.numpy()
+        img = synth.as_numpy_images(b)
+        ref = oracle.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"], max_iter=300,
+                               min_delta=0.0, min_step=1e-13)
+        from tests.parity import determined
+        det = determined(b, ref) if name == "ell32" else np.ones(n, bool)
+        errs = []
+        for s in np.nonzero(det)[0]:
+            off = int(d["offsets"][s])
+            W, H = int(d["dims"][s, 0]), int(d["dims"][s, 1])
+            gs = img[off:off + W * H].astype(np.float64)
+            up = np.concatenate([gp[s].numpy(), [ga[s], gb[s], 0.0]]).astype(np.float64)
+            ro = oracle.backward(int(d["model"][s]), W, H, gs, ref["params"][s], ref["alpha"][s],
+                                 ref["beta"][s], up)
+            assert ro is not None
+            errs.append(np.linalg.norm(grad[off:off + W * H] - ro) / np.linalg.norm(ro))
+        errs = np.array(errs)
+        print(f"{name} backward without chi2 upstream: {len(errs)} spots, median "
+              f"{np.median(errs):.2e}, max {errs.max():.2e}")
+        assert np.mean(errs <= 1e-4) >= 0.999 and np.median(errs) <= 1e-5
+
+
 def test_backward_matches_finite_differences_1024_iso16():
     """The backward workload's stated check: the GPU pixel gradient (forward and backward
     kernels, tight FP32 stop) of the first 1,024 16x16 isotropic spots against central

@@ -229,7 +229,9 @@ int64_t fit_spots_noalloc_max_spots(void);
  *   images, dtype, image_elems, offsets, roi_dims, model, n   as passed to fit_spots
  *   params, alpha, beta, state                                the fit_spots outputs
  *   grad_params [n][4], grad_alpha [n], grad_beta [n], grad_chi2 [n]   upstream (device;
- *                                                             any may be NULL = zero)
+ *                                                             any may be NULL = zero; with
+ *                                                             grad_chi2 NULL the pixels are
+ *                                                             read once instead of twice)
  *   grad_images  device float32 buffer of image_elems elements; the pixels of every valid
  *                spot are written (zeros for spots whose state is not a converged one
  *                or whose system M is singular); other elements are left untouched.

@@ -40,3 +40,23 @@ def test_fp32_model_values_alone_move_flat_fits_beyond_the_bar(oracle_mod, name)
     assert m["class_agree_wp"] == 1.0 and m["bar_wp"] >= 0.999
     assert m["class_agree"] >= 0.999
     assert m["bar_converged"] < 0.999
+
+
+def test_fits_do_not_move_with_fp32_ulp_changes_of_the_start(oracle_mod):
+    """The contrast: moving every start value by 16 FP32 ulps (random directions) leaves all
+    converged ell32 fits inside the bar, so the end points are not fragile to the path as
+    such; what moves them is the precision of the model values (the test above)."""
+    b = synth.make_workload("ell32", 20000)
+    d = b.numpy()
+    img = synth.as_numpy_images(b)
+    ref = oracle_mod.fit_spots(img, d["offsets"], d["dims"], d["init"], d["model"])
+    rng = np.random.default_rng(1)
+    init = d["init"].copy()
+    for _ in range(16):
+        init = np.nextafter(init, np.where(rng.random(init.shape) < 0.5, -np.inf, np.inf)
+                            ).astype(np.float32)
+    alt = oracle_mod.fit_spots(img, d["offsets"], d["dims"], init, d["model"])
+    m = compare(alt, ref, d["dims"], determined(b, ref))
+    print(f"ell32, start values moved by 16 ulps: class {m['class_agree']:.5f}, converged "
+          f"within the bar {m['bar_converged']:.5f}")
+    assert m["class_agree"] >= 0.9999 and m["bar_converged"] >= 0.9999

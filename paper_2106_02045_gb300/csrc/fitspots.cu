@@ -1693,7 +1693,7 @@ __device__ __forceinline__ void batched_drain(const FitArgs &a, const int cls, c
       }
     }
     if (!__ballot_sync(full, active)) break;
-    // slots to evaluate this round: the active ones without a pending re-solve
+    // slots to evaluate now: the active ones without a pending re-solve
     const unsigned amask =
         __ballot_sync(full, active && lane < kSlots && !(STI(SFLAGS, lane) & kResolve));
     __syncwarp();

@@ -2163,12 +2163,14 @@ bool config_fits(int cfg, int cls) {
 
 // Built-in choice per size class (lanes, cols, batched) for a class that runs alone
 // (fit_spots_uniform, fit_spots_per_class), from timing every usable configuration on
-// 131,072-spot samples at each class's bound size on a GB300: the batched kernel wins except
-// at 24 x 16 and 24 x 32, where three columns per lane leave too few resident warps.
+// 131,072-spot samples at each class's bound size on a GB300 (the autotuner's choice): the
+// batched kernels win except at 24 x 24, where the per-spot one-column kernel does; for
+// widths 17..24 with more than 8 rows the one-column 32-lane kernels beat three columns per
+// lane, whose larger LM step and register needs leave too few resident warps.
 constexpr int kDefaultCfg[kNumClasses - 1][3] = {
     {8, 1, 1},  {8, 1, 1},  {8, 1, 1},  {8, 1, 1},    // width bound 8, rows 8..32
     {16, 1, 1}, {16, 1, 1}, {16, 1, 1}, {16, 1, 1},   // 16
-    {8, 3, 1},  {8, 3, 0},  {8, 3, 1},  {8, 3, 0},    // 24
+    {8, 3, 1},  {32, 1, 1}, {32, 1, 0}, {32, 1, 1},   // 24
     {16, 2, 1}, {32, 1, 1}, {32, 1, 1}, {32, 1, 1}};  // 32
 
 int default_config(int cls) {

@@ -18,10 +18,10 @@
 // combined with a pairwise tree through shared memory (no atomics, fixed order, so a
 // spot's result does not depend on its neighbours). The LM bookkeeping (Eq. 6 2x2
 // solve, J^T J assembly, diagonally scaled Cholesky of Eq. 14, damping, stop tests) runs
-// in FP32; the 2x2 amplitude solve and the damped solve are redone in FP64 where FP32
-// cancellation would cost them 10 bits or more (FP64 runs at about 1/64 of the FP32 rate
-// on this GPU, so it is kept to those systems), and a damped system that FP32 rounding
-// leaves not positive definite gets more damping instead of ending the fit.
+// in FP32; the 2x2 amplitude solve is redone in FP64 where its determinant cancels by a
+// factor above 1024, the damped solve where the FP32 factorisation fails (FP64 runs at about
+// 1/74 of the FP32 rate on this GPU, so it is kept to those systems), and a damped system
+// that rounding leaves not positive definite gets more damping instead of ending the fit.
 //
 // Gradient. With alpha^, beta^ at their optimum, sum_i r_i = sum_i r_i f_i = 0 (Eq. 4), so
 // J^T r = alpha^ sum_i r_i df_i/dp_j (the other two terms of Eq. 9 vanish), and

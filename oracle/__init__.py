@@ -5,9 +5,10 @@ baseline leg of ``bench.py`` may import this package; the library itself never d
 The arithmetic lives in ``fitspots_oracle.c`` (plain C, double precision, one spot at a
 time, OpenMP across spots); this module compiles it with gcc and marshals numpy arrays.
 
-parity unpinned: the limit() box, the normalised chi^2 divisor, the maxError default and
-the damping schedule's constants are conventions or readings that no printed value pins
-(see the header of ``fitspots_oracle.c``). The NO_DECREASE exit and the order of the stop
+parity unpinned: the limit() box, the maxError default and the damping schedule's
+constants are conventions or readings that no printed value pins (see the header of
+``fitspots_oracle.c``); the normalised chi^2 divisor is pinned statistically (the unbiased
+residual variance). The NO_DECREASE exit and the order of the stop
 tests are pinned by the paper's stop-condition shares through a second build of the same
 source with the paper's FP32 chi^2 (``paper_arithmetic=True``).
 """

@@ -43,9 +43,10 @@
  *       comparison fits keep both sides at most 32.
  * Pixel i of a W x H spot sits at x_i = i mod W, y_i = floor(i / W) (row-major).
  *
- * parity unpinned: limit() bounds (R8), normalised chi^2 (R9) and the maxError default
- * (R7) are conventions; the CUDA path follows the same readings, nothing in the paper
- * fixes them. The damping schedule (R11) is not pinned by a printed value either: changes
+ * parity unpinned: limit() bounds (R8) and the maxError default (R7) are conventions; the
+ * CUDA path follows the same readings, nothing in the paper fixes them. The normalised chi^2
+ * (R9) is pinned statistically: chi^2 / (N - P - 2) is the unbiased residual variance, mean
+ * 1 for unit white noise (tests/test_oracle_pins.py). The damping schedule (R11) is not pinned by a printed value either: changes
  * to it leave the fits and the paper's statistics unchanged (only the GPU-vs-oracle
  * iteration histograms compare it). The NO_DECREASE exit (R4), the escalation loop's exit
  * and the order of the stop tests are pinned by the stop-condition shares the paper

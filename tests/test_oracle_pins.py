@@ -521,3 +521,40 @@ def test_paper_arithmetic_reproduces_the_stop_conditions(oracle_mod):
     conv = np.isin(paper["state"], (1, 2, 4)) & np.isin(fp64["state"], (1, 2, 4))
     dx = np.abs(paper["params"][conv, :2] - fp64["params"][conv, :2])
     assert np.median(dx) < 1e-3 and np.percentile(dx, 99) < 2e-2
+
+
+@pytest.mark.parametrize("model,S", [(0, 9), (1, 15)])
+def test_normalised_chi2_is_the_residual_variance(oracle_mod, model, S):
+    """Reading R9 (the paper names a normalised chi^2 without its divisor): chi^2 / (N - P - 2)
+    is the unbiased estimate of the pixel noise variance at the minimum over the P shape
+    parameters and the two amplitudes. With white Gaussian noise of variance 1 its mean over
+    many well-determined fits is 1 to within sampling error, which the other candidate
+    divisors (N, N - P) miss by several standard errors."""
+    rng = np.random.default_rng(91 + S)
+    n, N = 6000, S * S
+    P = 3 if model == 0 else 4
+    ys, xs = np.mgrid[0:S, 0:S]
+    imgs, inits = [], []
+    for _ in range(n):
+        c = (S - 1) / 2
+        p = np.array([c + rng.uniform(-0.5, 0.5), c + rng.uniform(-0.5, 0.5),
+                      rng.uniform(1.2, 2.0), rng.uniform(1.2, 2.0)])
+        if model == 0:
+            p[3] = p[2]
+        f = np.exp(-0.5 * ((xs - p[0]) / p[2]) ** 2 - 0.5 * ((ys - p[1]) / p[3]) ** 2)
+        imgs.append((400.0 * f + 20.0 + rng.normal(size=f.shape)).ravel())
+        inits.append(p * np.array([1.0, 1.0, 1.05, 0.95]))
+    img = np.concatenate(imgs)
+    out = oracle_mod.fit_spots(img, np.arange(n, dtype=np.int64) * N,
+                               np.tile(np.array([[S, S]], np.int32), (n, 1)),
+                               np.array(inits, np.float32), np.full(n, model, np.uint8),
+                               max_iter=100, min_delta=0.0, min_step=1e-10)
+    ok = np.isin(out["state"], (1, 2, 4))
+    assert ok.mean() > 0.99
+    c2n = out["chi2"][ok]
+    se = c2n.std() / np.sqrt(c2n.size)
+    mean = c2n.mean()
+    print(f"model {model}, {S}x{S}: mean chi2/(N-P-2) {mean:.4f} +- {se:.4f}")
+    assert abs(mean - 1.0) < 4 * se
+    for dof in (N, N - P):   # the alternatives are off by (P + 2) / N or 2 / N
+        assert abs(mean * (N - P - 2) / dof - 1.0) > 4 * se

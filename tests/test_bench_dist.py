@@ -110,3 +110,21 @@ def test_paper_protocol_section_with_a_stub(monkeypatch):
     assert [(r["S"], r["batch"], r["calls"]) for r in out["rows"]] == [(9, 10, 3), (9, 100, 2)]
     assert all(r["converged_fraction"] == 1.0 and r["fits_per_s"] > 0 for r in out["rows"])
     assert calls == [(9, 10)] * 4 + [(9, 100)] * 3
+
+
+def test_profile_key_ignores_comments_and_tracks_code(tmp_path):
+    """The ncu summaries are tied to the CUDA source by a hash of its code without comments:
+    editing a comment keeps the key (and the DRAM traffic the bench reports), changing code
+    drops it."""
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("// header\nint f(int x) {  // doubled\n  return 2 * x;\n}\n")
+    key = bench.code_hash(src)
+    src.write_text("// another header\n\nint f(int x) {  // twice x\n  return 2 * x;\n}\n")
+    assert bench.code_hash(src) == key
+    prof = tmp_path / "p.md"
+    prof.write_text(f"code_sha256_16: {key}\ntraffic_bytes_per_full_launch: 123 (x)\n")
+    assert bench._traffic_from_profile(prof, src) == 123.0
+    src.write_text("int f(int x) {\n  return 3 * x;\n}\n")
+    assert bench.code_hash(src) != key
+    assert bench._traffic_from_profile(prof, src) is None

@@ -266,3 +266,38 @@ def test_tie_refinement_equals_the_chi2_difference(oracle_mod, model):
         delta = (dh * (dh - 2 * rb)).sum()
         exact = et["chi2"] - eb["chi2"]
         assert abs(delta - exact) <= 1e-7 * abs(exact) + 1e-12 * eb["chi2"]
+
+
+def test_fp32_separable_normal_matrix_loses_digits_only_on_flat_profiles(oracle_mod):
+    """Why FP32 fits part from the FP64 oracle on flat chi^2 surfaces: the separable J^T J is a
+    small difference of large products of 1-D moments when the profile is nearly flat over
+    the ROI (widths near the ROI size), so the same formulas evaluated from FP32-rounded sums
+    in FP32 lose digits there and not on compact spots. (The GPU kernels form these sums and
+    this assembly in FP32.)"""
+    rng = np.random.default_rng(77)
+    W = H = 32
+    ys, xs = np.mgrid[0:H, 0:W]
+
+    def rel_err(s_true):
+        errs = []
+        for _ in range(20):
+            p = np.array([15.5 + rng.uniform(-1, 1), 15.5 + rng.uniform(-1, 1),
+                          s_true * rng.uniform(0.9, 1.1), s_true * rng.uniform(0.9, 1.1)])
+            f = np.exp(-0.5 * ((xs - p[0]) / p[2]) ** 2 - 0.5 * ((ys - p[1]) / p[3]) ** 2)
+            g = rng.poisson(60.0 * f + 300.0).astype(np.float64).ravel()
+            ref = oracle_mod.evaluate(ELL, W, H, g, p)
+            shift = float(np.rint(ref["beta"]))
+            X, Y, T, alpha, bp, Gs, F, FF, N, R = _sums(g, W, H, 32, p, False, shift)
+            f32 = lambda v: ({k: np.float32(x) for k, x in v.items()} if isinstance(v, dict)
+                             else np.float32(v))
+            A32, _ = _assemble(f32(X), f32(Y), f32(T), f32(alpha), f32(bp), f32(Gs), f32(F),
+                               f32(FF), N, R, p.astype(np.float32), False)
+            d = np.abs(np.diag(A32) - np.diag(ref["A"])) / np.abs(np.diag(ref["A"]))
+            errs.append(d.max())
+        return float(np.median(errs))
+
+    compact, flat = rel_err(2.0), rel_err(20.0)
+    print(f"FP32 separable J^T J, max relative diagonal error: compact spots {compact:.1e}, "
+          f"flat spots {flat:.1e}")
+    assert compact < 1e-5
+    assert flat > 10 * compact   # measured: about 35 times
